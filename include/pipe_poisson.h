@@ -1,0 +1,194 @@
+/*
+ * pipe_poisson.h -- C ABI of the GB300 open-rectangular-pipe Poisson solver.
+ *
+ * The solver computes, on a mesh x_i = x0 + i*hx, y_j = y0 + j*hy, z_k = k*hz
+ * (i < nx, j < ny, k < nz) inside the pipe (0,a) x (0,b), open in z:
+ *
+ *     phi_ijk = hx*hy*hz * sum_{i'j'k'} rho_{i'j'k'} G(x_i, x_i', y_j, y_j', z_k - z_k')
+ *
+ * (the discretised Green-function integral, Sec. 1 Eq. 1 and Eq. 4), with G
+ * the pipe Green function of Sec. 2 Eq. 7-9 (ordinary point Green function) or
+ * its longitudinally integrated form of Sec. 3 Eq. 15-16 (IGF).  The mode
+ * series is truncated at m <= modes_m, n <= modes_n (Sec. 4 uses 20).  G is
+ * normalised so that G -> 1/r near the source (series prefactor 8*pi/(a*b) for
+ * the sine form, 2*pi/(a*b) for the cosine form R); multiply phi by
+ * 1/(4*pi*eps0) for SI units.  A free-space handle (Eq. 3, Eq. 5, the Hockney
+ * method) is also provided for comparison.
+ *
+ * Method (Sec. 2 Eq. 10, Appendix A): zero-padding to (2nx, 2ny, 2nz), FFTs
+ * whose direction is chosen per dimension so that x and y realise convolution
+ * (x - x') or correlation (x + x'), a pointwise product with the transformed
+ * Green function computed once at setup (Sec. 5), an inverse transform, crop.
+ *
+ * Conventions common to every entry point
+ *  - Returns a status code (PIPE_OK = 0).  No C++ exception crosses the ABI.
+ *  - Densities and potentials are device arrays in C order [nx][ny][nz]
+ *    (z contiguous), of the handle's dtype, 16-byte aligned.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous and stream-ordered unless stated otherwise.
+ *  - A handle owns device memory (Green spectrum, workspace, tables) on the
+ *    device that was current at setup; it must not be used on two streams at
+ *    the same time (the workspace is shared).
+ */
+#ifndef PIPE_POISSON_H
+#define PIPE_POISSON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PIPE_OK           0
+#define PIPE_EINVAL       1  /* bad argument: sizes, spacings, geometry, null or misaligned pointer */
+#define PIPE_ENOMEM       2  /* device or host allocation failed */
+#define PIPE_EUNSUPPORTED 3  /* valid request outside what this build implements */
+#define PIPE_ECUDA        4  /* a CUDA call or kernel launch failed */
+#define PIPE_ETIMEOUT     5  /* a bounded device-side wait gave up (batched launch) */
+#define PIPE_ENODEVICE    6  /* no CUDA device / driver available */
+
+/* dtypes */
+#define PIPE_F32 0
+#define PIPE_F64 1
+
+/* Green function kinds for pipe_green_setup's `igf` argument */
+#define PIPE_GREEN_ORDINARY 0   /* Eq. 9: exp(-kappa |w|) */
+#define PIPE_GREEN_IGF      1   /* Eq. 16: g_z(w) of Eq. 15 */
+
+/* Pipe cross-section (0,a) x (0,b) (Sec. 2) and the mesh origin.
+ * x0, y0: coordinates of mesh node (0,0).  modes_m, modes_n: series truncation. */
+typedef struct {
+  double a, b;
+  double x0, y0;
+  int modes_m, modes_n;
+} pipe_geometry;
+
+/* Physical mesh nx x ny x nz with spacings hx, hy, hz, and the arithmetic type
+ * of the solve (PIPE_F32 or PIPE_F64).  The Green function is always tabulated
+ * and transformed in FP64; the F32 path uses an FP32 copy of its spectrum. */
+typedef struct {
+  int nx, ny, nz;
+  double hx, hy, hz;
+  int dtype;
+} pipe_grid;
+
+typedef struct pipe_handle pipe_handle;
+
+/* Tabulate the pipe Green function R (Eq. 9, or R_int of Eq. 16 when igf = 1)
+ * on the doubled grid and transform it (Sec. 2, after Eq. 10; Sec. 5: computed
+ * once, stored, reused).  Allocates every device buffer the solves need.
+ *
+ * Supported in this build: nx == ny in {16, 32, 64, 128}; nz in
+ * {32, 64, 128, 256, 512, 1024}; meshes that span the pipe (nx*hx == a,
+ * ny*hy == b to 1e-12 relative) with 2*x0/hx and 2*y0/hy integers (cell-centred
+ * x0 = hx/2, or a node on the wall x0 = 0); 1 <= modes <= 4096.
+ * Errors: PIPE_EINVAL (non-positive sizes or spacings, mesh not inside the
+ * pipe, bad dtype / igf, out == NULL), PIPE_EUNSUPPORTED (other sizes or
+ * meshes), PIPE_ENOMEM, PIPE_ECUDA.  On error *out is set to NULL.
+ * Synchronous (returns once the spectrum is ready). */
+int pipe_green_setup(const pipe_geometry* geometry, const pipe_grid* grid, int igf,
+                     pipe_handle** out);
+
+/* Free-space (Hockney) comparison handle: Eq. 5 with G = 1/r (Eq. 3) tabulated
+ * on the doubled grid with convolution offsets in x, y and z.  The paper does
+ * not give G(0,0,0); `self_value` supplies it (<= 0 selects 1/min(hx,hy,hz)).
+ * Same size limits and errors as pipe_green_setup (no geometry needed). */
+int pipe_free_space_setup(const pipe_grid* grid, double self_value, pipe_handle** out);
+
+/* phi = A rho (the forward solve of Eq. 10).  rho, phi: device [nx][ny][nz]
+ * arrays of the handle's dtype; phi may alias rho (in-place).  Errors:
+ * PIPE_EINVAL (null handle or pointer, misaligned pointer), PIPE_ECUDA. */
+int pipe_poisson_solve(pipe_handle* h, const void* rho, void* phi, void* stream);
+
+/* drho = A^T dphi: the transposed operator, applied as the transposed chain of
+ * Eq. 10 (the final-direction transforms of each term first, the product with
+ * the same Green spectra, then the forward transform, crop).  Because
+ * G(r, r') = G(r', r) (Eq. 7), A^T = A; this entry point is what gradients
+ * (dW/drho, backward passes) call.  Same arguments and errors as the solve. */
+int pipe_poisson_adjoint(pipe_handle* h, const void* dphi, void* drho, void* stream);
+
+/* Same as pipe_poisson_solve but rho_host / phi_host are HOST arrays: the
+ * library copies rho to the device, solves and copies phi back on `stream`,
+ * then synchronises the stream.  Device staging buffers are allocated on the
+ * first call and owned by the handle.  Host memory should be pinned for full
+ * copy bandwidth (pageable memory works, slower). */
+int pipe_poisson_solve_host(pipe_handle* h, const void* rho_host, void* phi_host, void* stream);
+
+/* n independent solves (different grids and geometries) in one persistent
+ * kernel launch that walks a work list of (solve, stage, tile) items; each
+ * stage of a solve waits, with a bounded spin, for the previous stage of the
+ * same solve.  All handles must share one dtype and device, and must not be
+ * used concurrently elsewhere.  A wait that gives up records PIPE_ETIMEOUT in
+ * the batch status (read with pipe_batch_status after the stream completes).
+ * Capturable in a CUDA graph after the first call with the same handle set
+ * (the first call builds and uploads the work list; later calls reuse it).
+ * Errors: PIPE_EINVAL (n < 1, null arrays), PIPE_EUNSUPPORTED (mixed dtypes
+ * or devices), PIPE_ENOMEM, PIPE_ECUDA. */
+int pipe_poisson_solve_batched(pipe_handle* const* handles, const void* const* rho,
+                               void* const* phi, int n, void* stream);
+
+/* Device-side status of the last batched launch that used `handles[0]`'s
+ * batch plan: PIPE_OK or PIPE_ETIMEOUT.  Synchronous (copies one word). */
+int pipe_batch_status(pipe_handle* const* handles, int n);
+
+/* Copy the handle's FP64 Green spectrum (the real octant g[kz][ky][kx],
+ * kz <= nz, ky <= ny, kx <= nx, already multiplied by hx*hy*hz/(8*nx*ny*nz))
+ * to host memory `out` of `count` doubles; count must equal
+ * (nx+1)*(ny+1)*(nz+1).  Synchronous.  For inspection and tests. */
+int pipe_green_spectrum(pipe_handle* h, double* out, size_t count);
+
+/* Stages of the solve, exposed for inspection and per-kernel tests.  `spec`
+ * is a caller-owned device array of (nz+1)*nx*ny complex values of the
+ * handle's dtype (interleaved re, im), laid out [kz][i][j].
+ *   z_forward : spec = the (2nz)-point DFT along z of the zero-padded rho,
+ *               kz = 0..nz (direction e^{-}, or e^{+} when adjoint != 0)
+ *   transverse: in place on spec -- padded x,y transforms, Green product,
+ *               cropped inverse x,y transforms (adjoint: transposed chain)
+ *   z_inverse : phi = the unnormalised (2nz)-point inverse along z of the
+ *               Hermitian half spectrum, first nz outputs */
+int pipe_stage_z_forward(pipe_handle* h, const void* rho, void* spec, int adjoint, void* stream);
+int pipe_stage_transverse(pipe_handle* h, void* spec, int adjoint, void* stream);
+int pipe_stage_z_inverse(pipe_handle* h, const void* spec, void* phi, int adjoint, void* stream);
+
+/* Time the kernel variants available for this handle's sizes on `stream` and
+ * keep the fastest (per size and dtype, shared by all handles of that shape in
+ * this process).  Synchronous; uses the handle's workspace as scratch.  If the
+ * environment variable PIPE_TUNE_CACHE names a file, results are read from and
+ * appended to it. */
+int pipe_autotune(pipe_handle* h, void* stream);
+
+/* Cloud-in-cell deposit of n macroparticles (positions xyz[n][3], FP64 or FP32
+ * per the handle's dtype, charge q each) onto the handle's mesh nodes:
+ * rho[i][j][k] += q * w / (hx*hy*hz), w the trilinear weight of node (i,j,k).
+ * Particles outside the mesh's node range contribute only to the nodes that
+ * exist.  rho must be zeroed by the caller.  Device arrays. */
+int pipe_cic_deposit(pipe_handle* h, const void* xyz, int64_t n, double q, void* rho,
+                     void* stream);
+
+/* Adjoint of the deposit with respect to the positions: for a cotangent
+ * grad_rho on the mesh, grad_xyz[p][d] = q/(hx*hy*hz) * sum_nodes grad_rho *
+ * d w / d x_d  (derivative of the trilinear weights).  Device arrays. */
+int pipe_cic_gather_grad(pipe_handle* h, const void* xyz, int64_t n, double q,
+                         const void* grad_rho, void* grad_xyz, void* stream);
+
+/* Release everything the handle owns (synchronises the device first).
+ * NULL is ignored. */
+void pipe_green_destroy(pipe_handle* h);
+
+/* Static description of a status code. */
+const char* pipe_strerror(int status);
+
+/* Host-only self test of the library's compile-time twiddle generator against
+ * the C library's cos/sin; returns the maximum absolute error.  Needs no GPU. */
+double pipe_selftest_twiddles(void);
+
+/* Library version string. */
+const char* pipe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIPE_POISSON_H */

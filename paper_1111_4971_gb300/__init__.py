@@ -1,0 +1,213 @@
+"""GB300 open-rectangular-pipe Poisson solver (Ryne, FFT-based mixed convolutions
+and correlations; integrated Green function).
+
+Thin Python layer over the C ABI in ``include/pipe_poisson.h``: PyTorch
+supplies device memory and streams, every arithmetic step runs in the CUDA
+kernels of ``libpipepoisson.so``.
+
+    solver = PipeSolver(geometry, grid, igf=True, dtype=torch.float32)
+    phi = solver.solve(rho)                 # rho: cuda tensor [nx, ny, nz]
+    phi = PipePoissonFunction.apply(rho, solver)   # differentiable
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import PipeError, PipeGeometry, PipeGrid, check
+
+__all__ = ["PipeSolver", "PipePoissonFunction", "CICDeposit", "solve_batched", "PipeError",
+           "field_energy"]
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class PipeSolver:
+    """One Green-function setup (Sec. 5: computed once, reused) and its solves.
+
+    ``geometry``: object with a, b, x0, y0, modes_m, modes_n.
+    ``grid``: object with nx, ny, nz, hx, hy, hz.
+    ``dtype``: torch.float32 or torch.float64 (the solve's arithmetic type).
+    """
+
+    def __init__(self, geometry, grid, igf: bool = True, dtype=torch.float32, *,
+                 free_space: bool = False, self_value: float = 0.0, device=None):
+        self.lib = _lib.load()
+        self.dtype = dtype
+        self.shape = (int(grid.nx), int(grid.ny), int(grid.nz))
+        self.grid = grid
+        self.geometry = geometry
+        self.igf = bool(igf)
+        self.free_space = free_space
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        g = PipeGrid(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.hx), float(grid.hy),
+                     float(grid.hz), _lib.PIPE_F64 if dtype == torch.float64 else _lib.PIPE_F32)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            if free_space:
+                st = self.lib.pipe_free_space_setup(ctypes.byref(g), float(self_value), ctypes.byref(h))
+            else:
+                geo = PipeGeometry(float(geometry.a), float(geometry.b), float(geometry.x0),
+                                   float(geometry.y0), int(geometry.modes_m), int(geometry.modes_n))
+                st = self.lib.pipe_green_setup(ctypes.byref(geo), ctypes.byref(g), int(bool(igf)),
+                                               ctypes.byref(h))
+        check(st, "pipe_green_setup" if not free_space else "pipe_free_space_setup")
+        self.handle = h
+
+    # -- helpers ---------------------------------------------------------
+    def _check_field(self, t: torch.Tensor, name: str):
+        if t.dtype != self.dtype or t.device != self.device or tuple(t.shape) != self.shape \
+                or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.dtype} tensor of shape "
+                             f"{self.shape} on {self.device}")
+
+    def empty(self):
+        return torch.empty(self.shape, dtype=self.dtype, device=self.device)
+
+    # -- solves ----------------------------------------------------------
+    def solve(self, rho: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        self._check_field(rho, "rho")
+        out = self.empty() if out is None else out
+        self._check_field(out, "out")
+        check(self.lib.pipe_poisson_solve(self.handle, _ptr(rho), _ptr(out), _stream_ptr(stream)),
+              "pipe_poisson_solve")
+        return out
+
+    def adjoint(self, dphi: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        self._check_field(dphi, "dphi")
+        out = self.empty() if out is None else out
+        self._check_field(out, "out")
+        check(self.lib.pipe_poisson_adjoint(self.handle, _ptr(dphi), _ptr(out), _stream_ptr(stream)),
+              "pipe_poisson_adjoint")
+        return out
+
+    def solve_host(self, rho_host: torch.Tensor, phi_host: torch.Tensor | None = None, stream=None):
+        """Host arrays in, host array out (copies inside the call)."""
+        if rho_host.device.type != "cpu" or rho_host.dtype != self.dtype or not rho_host.is_contiguous():
+            raise ValueError("rho_host must be a contiguous CPU tensor of the solver dtype")
+        if phi_host is None:
+            phi_host = torch.empty(self.shape, dtype=self.dtype, pin_memory=True)
+        check(self.lib.pipe_poisson_solve_host(self.handle, _ptr(rho_host), _ptr(phi_host),
+                                               _stream_ptr(stream)), "pipe_poisson_solve_host")
+        return phi_host
+
+    def green_spectrum(self):
+        import numpy as np
+        nx, ny, nz = self.shape
+        out = np.empty((nz + 1, ny + 1, nx + 1), dtype=np.float64)
+        check(self.lib.pipe_green_spectrum(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           out.size), "pipe_green_spectrum")
+        return out
+
+    def spectrum_buffer(self):
+        nx, ny, nz = self.shape
+        cdt = torch.complex128 if self.dtype == torch.float64 else torch.complex64
+        return torch.empty((nz + 1, nx, ny), dtype=cdt, device=self.device)
+
+    def stage_z_forward(self, rho, spec, adjoint=False, stream=None):
+        check(self.lib.pipe_stage_z_forward(self.handle, _ptr(rho), _ptr(spec), int(adjoint),
+                                            _stream_ptr(stream)), "pipe_stage_z_forward")
+        return spec
+
+    def stage_transverse(self, spec, adjoint=False, stream=None):
+        check(self.lib.pipe_stage_transverse(self.handle, _ptr(spec), int(adjoint), _stream_ptr(stream)),
+              "pipe_stage_transverse")
+        return spec
+
+    def stage_z_inverse(self, spec, phi, adjoint=False, stream=None):
+        check(self.lib.pipe_stage_z_inverse(self.handle, _ptr(spec), _ptr(phi), int(adjoint),
+                                            _stream_ptr(stream)), "pipe_stage_z_inverse")
+        return phi
+
+    def autotune(self, stream=None):
+        check(self.lib.pipe_autotune(self.handle, _stream_ptr(stream)), "pipe_autotune")
+
+    def cic_deposit(self, xyz: torch.Tensor, charge: float, out: torch.Tensor | None = None,
+                    stream=None):
+        out = torch.zeros(self.shape, dtype=self.dtype, device=self.device) if out is None else out
+        xyz = xyz.contiguous()
+        check(self.lib.pipe_cic_deposit(self.handle, _ptr(xyz), xyz.shape[0], float(charge), _ptr(out),
+                                        _stream_ptr(stream)), "pipe_cic_deposit")
+        return out
+
+    def cic_gather_grad(self, xyz: torch.Tensor, charge: float, grad_rho: torch.Tensor, stream=None):
+        out = torch.empty_like(xyz)
+        check(self.lib.pipe_cic_gather_grad(self.handle, _ptr(xyz), xyz.shape[0], float(charge),
+                                            _ptr(grad_rho.contiguous()), _ptr(out), _stream_ptr(stream)),
+              "pipe_cic_gather_grad")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.pipe_green_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batched(solvers, rhos, phis, stream=None):
+    """n independent solves in one persistent launch (see pipe_poisson_solve_batched)."""
+    lib = _lib.load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    rs = (ctypes.c_void_p * n)(*[r.data_ptr() for r in rhos])
+    ps = (ctypes.c_void_p * n)(*[p.data_ptr() for p in phis])
+    check(lib.pipe_poisson_solve_batched(hs, rs, ps, n, _stream_ptr(stream)), "pipe_poisson_solve_batched")
+    return phis
+
+
+def batch_status(solvers):
+    lib = _lib.load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    return lib.pipe_batch_status(hs, n)
+
+
+class PipePoissonFunction(torch.autograd.Function):
+    """phi = A rho with backward g -> A^T g through the hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, rho, solver):
+        ctx.solver = solver
+        return solver.solve(rho.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.solver.adjoint(g.contiguous()), None
+
+
+class CICDeposit(torch.autograd.Function):
+    """rho = CIC(xyz) on the solver's mesh; backward gives d/dxyz through the
+    derivative of the trilinear weights."""
+
+    @staticmethod
+    def forward(ctx, xyz, solver, charge):
+        xyz = xyz.contiguous()
+        ctx.save_for_backward(xyz)
+        ctx.solver = solver
+        ctx.charge = charge
+        return solver.cic_deposit(xyz, charge)
+
+    @staticmethod
+    def backward(ctx, g):
+        (xyz,) = ctx.saved_tensors
+        return ctx.solver.cic_gather_grad(xyz, ctx.charge, g.contiguous()), None, None
+
+
+def field_energy(rho: torch.Tensor, phi: torch.Tensor) -> torch.Tensor:
+    """W = 1/2 sum rho phi."""
+    return 0.5 * (rho * phi).sum()

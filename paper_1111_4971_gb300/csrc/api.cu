@@ -1,0 +1,365 @@
+// C ABI of the pipe Poisson solver: handle management, validation, dispatch.
+// The declarations and their documentation are in include/pipe_poisson.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "../../include/pipe_poisson.h"
+#include "green_kernels.cuh"
+#include "handle.cuh"
+#include "solver.cuh"
+
+using namespace pp;
+
+namespace {
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int sub_fft_group(int L) { return (L <= 32) ? 4 : (L <= 128 ? 8 : (L <= 512 ? 16 : 32)); }
+
+// check that x is within rel of an integer; return it
+bool near_int(double x, int* out) {
+  const double r = std::nearbyint(x);
+  if (std::fabs(x - r) > 1e-9 * std::fmax(1.0, std::fabs(x))) return false;
+  *out = int(r);
+  return true;
+}
+
+int validate_grid(const pipe_grid* g) {
+  if (!g) return PIPE_EINVAL;
+  if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return PIPE_EINVAL;
+  if (!(g->hx > 0) || !(g->hy > 0) || !(g->hz > 0)) return PIPE_EINVAL;
+  if (!std::isfinite(g->hx) || !std::isfinite(g->hy) || !std::isfinite(g->hz)) return PIPE_EINVAL;
+  if (g->dtype != PIPE_F32 && g->dtype != PIPE_F64) return PIPE_EINVAL;
+  if (!is_pow2(g->nx) || !is_pow2(g->ny) || !is_pow2(g->nz)) return PIPE_EUNSUPPORTED;
+  if (g->nx != g->ny) return PIPE_EUNSUPPORTED;
+  if (g->nx < 16 || g->nx > 128) return PIPE_EUNSUPPORTED;
+  if (g->nz < 32 || g->nz > 1024) return PIPE_EUNSUPPORTED;
+  return PIPE_OK;
+}
+
+int status_of(cudaError_t e) {
+  if (e == cudaSuccess) return PIPE_OK;
+  if (e == cudaErrorMemoryAllocation) return PIPE_ENOMEM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return PIPE_ENODEVICE;
+  return PIPE_ECUDA;
+}
+
+size_t cplx_size(int dtype) { return dtype == PIPE_F64 ? 16 : 8; }
+
+// allocate everything but the Green spectrum; fill the twiddle tables
+int alloc_common(pipe_handle* h) {
+  const pipe_grid& g = h->grid;
+  const size_t oct = size_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+  const size_t work = size_t(g.nz + 1) * g.nx * g.ny * cplx_size(g.dtype);
+  cudaError_t e;
+  if ((e = cudaMalloc(&h->green64, oct * sizeof(double))) != cudaSuccess) return status_of(e);
+  if ((e = cudaMalloc(&h->green32, oct * sizeof(float))) != cudaSuccess) return status_of(e);
+  if ((e = cudaMalloc(&h->work, work)) != cudaSuccess) return status_of(e);
+  const int n = g.nx, Lz = g.nz / 2;
+  // float2 and double2 tables: tw_t (n), w2_t (2n), tw_z (nz/2), w2_z (2nz)
+  const size_t cnt = size_t(n) + 2 * n + Lz + 2 * g.nz;
+  if ((e = cudaMalloc(&h->tab32, cnt * sizeof(float2))) != cudaSuccess) return status_of(e);
+  if ((e = cudaMalloc(&h->tab64, cnt * sizeof(double2))) != cudaSuccess) return status_of(e);
+  h->tw_t32 = h->tab32; h->w2_t32 = h->tw_t32 + n; h->tw_z32 = h->w2_t32 + 2 * n; h->w2_z32 = h->tw_z32 + Lz;
+  h->tw_t64 = h->tab64; h->w2_t64 = h->tw_t64 + n; h->tw_z64 = h->w2_t64 + 2 * n; h->w2_z64 = h->tw_z64 + Lz;
+  cudaStream_t st = nullptr;
+  launch_tables<float2>(h->tw_t32, h->w2_t32, n, sub_fft_group(n), 2 * n, st);
+  launch_tables<float2>(h->tw_z32, h->w2_z32, Lz, sub_fft_group(Lz), 2 * g.nz, st);
+  launch_tables<double2>(h->tw_t64, h->w2_t64, n, sub_fft_group(n), 2 * n, st);
+  launch_tables<double2>(h->tw_z64, h->w2_z64, Lz, sub_fft_group(Lz), 2 * g.nz, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return status_of(e);
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return status_of(e);
+  return PIPE_OK;
+}
+
+void free_handle(pipe_handle* h) {
+  if (!h) return;
+  DeviceGuard dg(h->device);
+  cudaDeviceSynchronize();
+  cudaFree(h->green64); cudaFree(h->green32); cudaFree(h->work);
+  cudaFree(h->tab32); cudaFree(h->tab64);
+  cudaFree(h->stage_rho); cudaFree(h->stage_phi);
+  batch_release(h);
+  delete h;
+}
+
+template <typename T>
+SolveArgs<T> make_args(pipe_handle* h, const void* rho, void* phi, void* work);
+
+template <>
+SolveArgs<float> make_args<float>(pipe_handle* h, const void* rho, void* phi, void* work) {
+  SolveArgs<float> a;
+  a.rho = static_cast<const float*>(rho); a.phi = static_cast<float*>(phi);
+  a.work = static_cast<float2*>(work); a.green = h->green32;
+  a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32;
+  a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
+  a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  return a;
+}
+template <>
+SolveArgs<double> make_args<double>(pipe_handle* h, const void* rho, void* phi, void* work) {
+  SolveArgs<double> a;
+  a.rho = static_cast<const double*>(rho); a.phi = static_cast<double*>(phi);
+  a.work = static_cast<double2*>(work); a.green = h->green64;
+  a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64;
+  a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
+  a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  return a;
+}
+
+template <typename T>
+int run_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStream_t st) {
+  SolveArgs<T> a = make_args<T>(h, rho, phi, h->work);
+  cudaError_t e;
+  const int zw = h->plan.z_warps;
+  if ((e = launch_z<T>(true, zw, adjoint, a, st)) != cudaSuccess) return status_of(e);
+  if ((e = launch_transverse<T>(adjoint, a, st)) != cudaSuccess) return status_of(e);
+  if ((e = launch_z<T>(false, zw, adjoint, a, st)) != cudaSuccess) return status_of(e);
+  return PIPE_OK;
+}
+
+int check_ptr(const void* p) {
+  if (!p) return PIPE_EINVAL;
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return PIPE_EINVAL;
+  return PIPE_OK;
+}
+
+int finish_setup(pipe_handle* h, pipe_handle** out) {
+  *out = h;
+  return PIPE_OK;
+}
+
+}  // namespace
+
+namespace pp {
+int handle_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStream_t st) {
+  return h->grid.dtype == PIPE_F64 ? run_solve<double>(h, rho, phi, adjoint, st)
+                                   : run_solve<float>(h, rho, phi, adjoint, st);
+}
+}  // namespace pp
+
+extern "C" {
+
+const char* pipe_version(void) { return "pipe-poisson-gb300 0.1 (sm_103a)"; }
+
+const char* pipe_strerror(int s) {
+  switch (s) {
+    case PIPE_OK: return "ok";
+    case PIPE_EINVAL: return "invalid argument";
+    case PIPE_ENOMEM: return "out of memory";
+    case PIPE_EUNSUPPORTED: return "unsupported size or geometry";
+    case PIPE_ECUDA: return "CUDA error";
+    case PIPE_ETIMEOUT: return "device-side wait timed out";
+    case PIPE_ENODEVICE: return "no CUDA device";
+    default: return "unknown status";
+  }
+}
+
+double pipe_selftest_twiddles(void) {
+  // reference: long double cos/sin of the exactly reduced angle 2 pi (k mod n) / n
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  double worst = 0.0;
+  auto check = [&](long k, long n) {
+    long kr = k % n;
+    if (kr < 0) kr += n;
+    const long double ang = two_pi * (long double)kr / (long double)n;
+    worst = std::fmax(worst, std::fabs(ccos2pi(k, n) - double(cosl(ang))));
+    worst = std::fmax(worst, std::fabs(csin2pi(k, n) - double(sinl(ang))));
+  };
+  for (long n = 1; n <= 4096; n *= 2)
+    for (long k = -n; k <= 2 * n; ++k) check(k, n);
+  for (long n : {3L, 5L, 12L, 100L, 1000L})
+    for (long k = 0; k < n; ++k) check(k, n);
+  return worst;
+}
+
+int pipe_green_setup(const pipe_geometry* geom, const pipe_grid* grid, int igf, pipe_handle** out) {
+  if (!out) return PIPE_EINVAL;
+  *out = nullptr;
+  if (!geom) return PIPE_EINVAL;
+  if (igf != PIPE_GREEN_ORDINARY && igf != PIPE_GREEN_IGF) return PIPE_EINVAL;
+  int st = validate_grid(grid);
+  if (st == PIPE_EINVAL) return st;
+  if (!(geom->a > 0) || !(geom->b > 0) || !std::isfinite(geom->a) || !std::isfinite(geom->b))
+    return PIPE_EINVAL;
+  if (geom->modes_m < 1 || geom->modes_n < 1) return PIPE_EINVAL;
+  // the mesh must lie inside the pipe
+  const double tol = 1e-12;
+  if (geom->x0 < -tol * geom->a || geom->y0 < -tol * geom->b) return PIPE_EINVAL;
+  if (geom->x0 + (grid->nx - 1) * grid->hx > geom->a * (1 + tol)) return PIPE_EINVAL;
+  if (geom->y0 + (grid->ny - 1) * grid->hy > geom->b * (1 + tol)) return PIPE_EINVAL;
+  if (st != PIPE_OK) return st;
+  if (geom->modes_m > 4096 || geom->modes_n > 4096) return PIPE_EUNSUPPORTED;
+  // meshes spanning the pipe with integer correlation shifts
+  if (std::fabs(grid->nx * grid->hx - geom->a) > 1e-12 * geom->a) return PIPE_EUNSUPPORTED;
+  if (std::fabs(grid->ny * grid->hy - geom->b) > 1e-12 * geom->b) return PIPE_EUNSUPPORTED;
+  int sx = 0, sy = 0;
+  if (!near_int(2.0 * geom->x0 / grid->hx, &sx) || !near_int(2.0 * geom->y0 / grid->hy, &sy))
+    return PIPE_EUNSUPPORTED;
+
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return PIPE_ENODEVICE;
+  pipe_handle* h = new (std::nothrow) pipe_handle();
+  if (!h) return PIPE_ENOMEM;
+  cudaGetDevice(&h->device);
+  h->geom = *geom;
+  h->grid = *grid;
+  h->kind = igf;
+  h->sx = sx;
+  h->sy = sy;
+  h->images = 1;
+  h->plan = default_plan(grid->nz, grid->dtype == PIPE_F64);
+  if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
+  GreenSpec s;
+  s.nx = grid->nx; s.ny = grid->ny; s.nz = grid->nz;
+  s.hx = grid->hx; s.hy = grid->hy; s.hz = grid->hz;
+  s.a = geom->a; s.b = geom->b;
+  s.modes_m = geom->modes_m; s.modes_n = geom->modes_n;
+  s.igf = igf;
+  s.scale = grid->hx * grid->hy * grid->hz / (8.0 * grid->nx * grid->ny * grid->nz);
+  cudaError_t e = build_pipe_spectrum(s, h->green64, h->green32, nullptr);
+  if (e != cudaSuccess) { free_handle(h); return status_of(e); }
+  return finish_setup(h, out);
+}
+
+int pipe_free_space_setup(const pipe_grid* grid, double self_value, pipe_handle** out) {
+  if (!out) return PIPE_EINVAL;
+  *out = nullptr;
+  int st = validate_grid(grid);
+  if (st != PIPE_OK) return st;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return PIPE_ENODEVICE;
+  pipe_handle* h = new (std::nothrow) pipe_handle();
+  if (!h) return PIPE_ENOMEM;
+  cudaGetDevice(&h->device);
+  std::memset(&h->geom, 0, sizeof(h->geom));
+  h->grid = *grid;
+  h->kind = 2;
+  h->sx = h->sy = 0;
+  h->images = 0;
+  h->plan = default_plan(grid->nz, grid->dtype == PIPE_F64);
+  if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
+  if (!(self_value > 0)) self_value = 1.0 / std::fmin(grid->hx, std::fmin(grid->hy, grid->hz));
+  GreenSpec s;
+  s.nx = grid->nx; s.ny = grid->ny; s.nz = grid->nz;
+  s.hx = grid->hx; s.hy = grid->hy; s.hz = grid->hz;
+  s.a = s.b = 0; s.modes_m = s.modes_n = 0; s.igf = 0;
+  s.scale = grid->hx * grid->hy * grid->hz / (8.0 * grid->nx * grid->ny * grid->nz);
+  cudaError_t e = build_free_spectrum(s, self_value, h->green64, h->green32, nullptr);
+  if (e != cudaSuccess) { free_handle(h); return status_of(e); }
+  return finish_setup(h, out);
+}
+
+void pipe_green_destroy(pipe_handle* h) { free_handle(h); }
+
+int pipe_poisson_solve(pipe_handle* h, const void* rho, void* phi, void* stream) {
+  if (!h) return PIPE_EINVAL;
+  int st;
+  if ((st = check_ptr(rho)) != PIPE_OK || (st = check_ptr(phi)) != PIPE_OK) return st;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return PIPE_ECUDA;
+  return handle_solve(h, rho, phi, false, static_cast<cudaStream_t>(stream));
+}
+
+int pipe_poisson_adjoint(pipe_handle* h, const void* dphi, void* drho, void* stream) {
+  if (!h) return PIPE_EINVAL;
+  int st;
+  if ((st = check_ptr(dphi)) != PIPE_OK || (st = check_ptr(drho)) != PIPE_OK) return st;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return PIPE_ECUDA;
+  return handle_solve(h, dphi, drho, true, static_cast<cudaStream_t>(stream));
+}
+
+int pipe_poisson_solve_host(pipe_handle* h, const void* rho_host, void* phi_host, void* stream) {
+  if (!h || !rho_host || !phi_host) return PIPE_EINVAL;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return PIPE_ECUDA;
+  const size_t bytes = size_t(h->grid.nx) * h->grid.ny * h->grid.nz *
+                       (h->grid.dtype == PIPE_F64 ? 8 : 4);
+  cudaError_t e;
+  if (!h->stage_rho) {
+    if ((e = cudaMalloc(&h->stage_rho, bytes)) != cudaSuccess) return status_of(e);
+    if ((e = cudaMalloc(&h->stage_phi, bytes)) != cudaSuccess) return status_of(e);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((e = cudaMemcpyAsync(h->stage_rho, rho_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return status_of(e);
+  int s = handle_solve(h, h->stage_rho, h->stage_phi, false, st);
+  if (s != PIPE_OK) return s;
+  if ((e = cudaMemcpyAsync(phi_host, h->stage_phi, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return status_of(e);
+  return status_of(cudaStreamSynchronize(st));
+}
+
+int pipe_green_spectrum(pipe_handle* h, double* out, size_t count) {
+  if (!h || !out) return PIPE_EINVAL;
+  const size_t oct = size_t(h->grid.nx + 1) * (h->grid.ny + 1) * (h->grid.nz + 1);
+  if (count != oct) return PIPE_EINVAL;
+  DeviceGuard dg(h->device);
+  return status_of(cudaMemcpy(out, h->green64, oct * sizeof(double), cudaMemcpyDeviceToHost));
+}
+
+int pipe_stage_z_forward(pipe_handle* h, const void* rho, void* spec, int adjoint, void* stream) {
+  if (!h) return PIPE_EINVAL;
+  int st;
+  if ((st = check_ptr(rho)) != PIPE_OK || (st = check_ptr(spec)) != PIPE_OK) return st;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (h->grid.dtype == PIPE_F64)
+    e = launch_z<double>(true, h->plan.z_warps, adjoint != 0, make_args<double>(h, rho, nullptr, spec), s);
+  else
+    e = launch_z<float>(true, h->plan.z_warps, adjoint != 0, make_args<float>(h, rho, nullptr, spec), s);
+  return status_of(e);
+}
+
+int pipe_stage_transverse(pipe_handle* h, void* spec, int adjoint, void* stream) {
+  if (!h) return PIPE_EINVAL;
+  int st;
+  if ((st = check_ptr(spec)) != PIPE_OK) return st;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (h->grid.dtype == PIPE_F64)
+    e = launch_transverse<double>(adjoint != 0, make_args<double>(h, nullptr, nullptr, spec), s);
+  else
+    e = launch_transverse<float>(adjoint != 0, make_args<float>(h, nullptr, nullptr, spec), s);
+  return status_of(e);
+}
+
+int pipe_stage_z_inverse(pipe_handle* h, const void* spec, void* phi, int adjoint, void* stream) {
+  if (!h) return PIPE_EINVAL;
+  int st;
+  if ((st = check_ptr(spec)) != PIPE_OK || (st = check_ptr(phi)) != PIPE_OK) return st;
+  DeviceGuard dg(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  void* sp = const_cast<void*>(spec);
+  if (h->grid.dtype == PIPE_F64)
+    e = launch_z<double>(false, h->plan.z_warps, adjoint != 0, make_args<double>(h, nullptr, phi, sp), s);
+  else
+    e = launch_z<float>(false, h->plan.z_warps, adjoint != 0, make_args<float>(h, nullptr, phi, sp), s);
+  return status_of(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,294 @@
+// Setup kernels, all FP64: twiddle tables, tabulation of the pipe Green
+// function R / R_int (Sec. 2 Eq. 9, Sec. 3 Eq. 15-16) and of the free-space
+// 1/r (Eq. 3) on the doubled grid, and their forward transforms.
+//
+// Layout of the tabulated tables: octant [r][q][p], p = 0..nx, q = 0..ny,
+// r = 0..nz, holding R(p*hx, q*hy, r*hz).  The doubled-grid convolution table
+// (Fig. 1, Appendix A Eq. A.3) is the even extension of this octant (R is even
+// in each argument), and for a mesh that spans the pipe it is also the
+// correlation table up to a shift of 2*x0/hx samples.  The forward transform
+// of an even real table is real and even, so the transform of the whole
+// doubled table reduces to a weighted cosine transform (DCT-I) along each axis
+// of the octant:
+//     That(k) = T(0) + (-1)^k T(n) + 2 sum_{p=1}^{n-1} T(p) cos(pi p k / n).
+#include <cuda_runtime.h>
+
+#include "fft_common.cuh"
+#include "green_kernels.cuh"
+
+namespace pp {
+
+// tw[k1*G + t] = e^{-2 pi i t k1 / L}  (k1 < L/G, t < G);  w2[j] = e^{-2 pi i j / n2}
+template <typename V>
+__global__ void tables_kernel(V* tw, V* w2, int L, int G, int n2) {
+  using R = typename real_of<V>::type;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < L) {
+    const int k1 = idx / G, t = idx % G;
+    const long m = (long(t) * k1) % L;
+    double s, c;
+    sincospi(2.0 * double(m) / double(L), &s, &c);
+    tw[idx] = mk<V>(R(c), R(-s));
+  }
+  if (idx < n2) {
+    double s, c;
+    sincospi(2.0 * double(idx) / double(n2), &s, &c);
+    w2[idx] = mk<V>(R(c), R(-s));
+  }
+}
+
+template <typename V>
+void launch_tables(V* tw, V* w2, int L, int G, int n2, cudaStream_t st) {
+  const int n = L > n2 ? L : n2;
+  tables_kernel<V><<<(n + 255) / 256, 256, 0, st>>>(tw, w2, L, G, n2);
+}
+template void launch_tables<float2>(float2*, float2*, int, int, int, cudaStream_t);
+template void launch_tables<double2>(double2*, double2*, int, int, int, cudaStream_t);
+
+// cos(m pi p h / a), m = 1..M, p = 0..n  -> tab[(m-1)*(n+1) + p]
+__global__ void cos_table_kernel(double* tab, int M, int n, double h, double a) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * (n + 1)) return;
+  const int m = idx / (n + 1) + 1, p = idx % (n + 1);
+  tab[idx] = cospi(double(m) * double(p) * h / a);
+}
+
+// (x - 1 + e^{-x}) / x^2 without cancellation (Taylor series below 0.1)
+__device__ double xm1pe_over_x2(double x) {
+  if (x < 0.1) {
+    double term = 0.5, acc = 0.5;
+#pragma unroll 1
+    for (int j = 1; j < 16; ++j) {
+      term *= -x / double(j + 2);
+      acc += term;
+    }
+    return acc;
+  }
+  return (x + expm1(-x)) / (x * x);
+}
+
+// Z[(m-1)*N + (n-1)][r] = kappa_mn^{-1} * Z_mn(r*hz), r = 0..nz, where Z is
+// e^{-kappa |w|} (Eq. 9) or the longitudinal IGF g_z(w) (Eq. 15, evaluated in
+// its cancellation-free form: 4 sinh^2(kappa h/2) e^{-kappa|w|}/(kappa h)^2 for
+// |w| >= h, 2 (kappa h - 1 + e^{-kappa h})/(kappa h)^2 at w = 0).
+__global__ void z_profile_kernel(double* Z, int M, int N, int nz, double hz, double a, double b,
+                                 int igf) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N * (nz + 1)) return;
+  const int r = idx % (nz + 1);
+  const int mn = idx / (nz + 1);
+  const int m = mn / N + 1, n = mn % N + 1;
+  const double km = double(m) / a, kn = double(n) / b;
+  const double kap = M_PI * sqrt(km * km + kn * kn);
+  const double w = double(r) * hz;
+  double z;
+  if (!igf) {
+    z = exp(-kap * w);
+  } else {
+    const double x = kap * hz;
+    if (r == 0) {
+      z = 2.0 * xm1pe_over_x2(x);
+    } else {
+      const double s = sinh(0.5 * x);
+      z = 4.0 * s * s * exp(-kap * w) / (x * x);
+    }
+  }
+  Z[idx] = z / kap;
+}
+
+// U[m][q][r] = sum_n cy[n][q] Z[m][n][r]
+__global__ void contract_n_kernel(double* U, const double* cy, const double* Z, int M, int N,
+                                  int ny, int nz) {
+  const long idx = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long total = long(M) * (ny + 1) * (nz + 1);
+  if (idx >= total) return;
+  const int r = int(idx % (nz + 1));
+  const int q = int((idx / (nz + 1)) % (ny + 1));
+  const int m = int(idx / (long(nz + 1) * (ny + 1)));
+  double acc = 0.0;
+#pragma unroll 4
+  for (int n = 0; n < N; ++n) acc += cy[n * (ny + 1) + q] * Z[(long(m) * N + n) * (nz + 1) + r];
+  U[idx] = acc;
+}
+
+// T[r][q][p] = C * sum_m cx[m][p] U[m][q][r]
+__global__ void contract_m_kernel(double* T, const double* cx, const double* U, int M, int nx,
+                                  int ny, int nz, double C) {
+  const long idx = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long total = long(nx + 1) * (ny + 1) * (nz + 1);
+  if (idx >= total) return;
+  const int p = int(idx % (nx + 1));
+  const int q = int((idx / (nx + 1)) % (ny + 1));
+  const int r = int(idx / (long(nx + 1) * (ny + 1)));
+  double acc = 0.0;
+#pragma unroll 4
+  for (int m = 0; m < M; ++m)
+    acc += cx[m * (nx + 1) + p] * U[(long(m) * (ny + 1) + q) * (nz + 1) + r];
+  T[idx] = C * acc;
+}
+
+// free space: T[r][q][p] = 1/sqrt((p hx)^2 + (q hy)^2 + (r hz)^2), T[0][0][0] = self
+__global__ void free_octant_kernel(double* T, int nx, int ny, int nz, double hx, double hy,
+                                   double hz, double self) {
+  const long idx = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long total = long(nx + 1) * (ny + 1) * (nz + 1);
+  if (idx >= total) return;
+  const int p = int(idx % (nx + 1));
+  const int q = int((idx / (nx + 1)) % (ny + 1));
+  const int r = int(idx / (long(nx + 1) * (ny + 1)));
+  const double u = p * hx, v = q * hy, w = r * hz;
+  T[idx] = (p == 0 && q == 0 && r == 0) ? self : rsqrt(u * u + v * v + w * w);
+}
+
+__global__ void cos_pi_table_kernel(double* c, int n) {   // c[j] = cos(pi j / n), j < 2n
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < 2 * n) c[j] = cospi(double(j) / double(n));
+}
+
+// Weighted cosine transform along one axis, batched:
+//   out[b*bs + k*ks + l*ls] = sum_{p=0}^{n} w_p cos(pi p k/n) in[b*bs + p*ks + l*ls]
+// w_0 = w_n = 1, otherwise 2; k = 0..n, l < nl, b < nb.  64x64 output tiles,
+// 16-deep slices of p in shared memory, 4x4 outputs per thread.
+__global__ void __launch_bounds__(256) dct1_axis_kernel(const double* __restrict__ in,
+                                                        double* __restrict__ out, int n, int nl,
+                                                        long ks, long ls, long bs,
+                                                        const double* __restrict__ cosn) {
+  __shared__ double Ws[16][65];
+  __shared__ double Xs[16][65];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int k0 = blockIdx.y * 64, l0 = blockIdx.x * 64;
+  const long boff = long(blockIdx.z) * bs;
+  double acc[4][4] = {};
+  const bool p_fast = (ks == 1);
+  for (int p0 = 0; p0 <= n; p0 += 16) {
+    for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
+      int pp, ll;
+      if (p_fast) { pp = idx % 16; ll = idx / 16; } else { pp = idx / 64; ll = idx % 64; }
+      const int p = p0 + pp, l = l0 + ll;
+      Xs[pp][ll] = (p <= n && l < nl) ? in[boff + p * ks + l * ls] : 0.0;
+      const int kk = idx % 64, pq = idx / 64;
+      const int pk = p0 + pq, k = k0 + kk;
+      double wv = 0.0;
+      if (pk <= n && k <= n) {
+        const double wp = (pk == 0 || pk == n) ? 1.0 : 2.0;
+        wv = wp * cosn[(long(pk) * k) % (2 * n)];
+      }
+      Ws[pq][kk] = wv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int pp = 0; pp < 16; ++pp) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = Ws[pp][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Xs[pp][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = k0 + ty + 16 * i;
+    if (k > n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = l0 + tx + 16 * j;
+      if (l < nl) out[boff + k * ks + l * ls] = acc[i][j];
+    }
+  }
+}
+
+__global__ void finalize_kernel(const double* T, double* g64, float* g32, long total, double scale) {
+  const long idx = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const double v = T[idx] * scale;
+  g64[idx] = v;
+  g32[idx] = float(v);
+}
+
+static inline unsigned nblk(long total, int bs) { return unsigned((total + bs - 1) / bs); }
+
+// Forward transform of an even real octant table T (in place through `tmp`):
+// DCT-I along x (p), then y (q), then z (r).  Result in T.
+static cudaError_t octant_transform(double* T, double* tmp, double* cosbuf, int nx, int ny, int nz,
+                                    cudaStream_t st) {
+  const long sx = 1, sy = nx + 1, sz = long(nx + 1) * (ny + 1);
+  // x axis: lines = q (stride sy), batches = r (stride sz)
+  cos_pi_table_kernel<<<nblk(2 * nx, 256), 256, 0, st>>>(cosbuf, nx);
+  {
+    dim3 grid(nblk(ny + 1, 64), nblk(nx + 1, 64), nz + 1);
+    dct1_axis_kernel<<<grid, 256, 0, st>>>(T, tmp, nx, ny + 1, sx, sy, sz, cosbuf);
+  }
+  // y axis: lines = p (stride 1), batches = r
+  cos_pi_table_kernel<<<nblk(2 * ny, 256), 256, 0, st>>>(cosbuf, ny);
+  {
+    dim3 grid(nblk(nx + 1, 64), nblk(ny + 1, 64), nz + 1);
+    dct1_axis_kernel<<<grid, 256, 0, st>>>(tmp, T, ny, nx + 1, sy, 1, sz, cosbuf);
+  }
+  // z axis: lines = (q, p) flattened (stride 1), one batch
+  cos_pi_table_kernel<<<nblk(2 * nz, 256), 256, 0, st>>>(cosbuf, nz);
+  {
+    dim3 grid(nblk(sz, 64), nblk(nz + 1, 64), 1);
+    dct1_axis_kernel<<<grid, 256, 0, st>>>(T, tmp, nz, int(sz), sz, 1, 0, cosbuf);
+  }
+  return cudaMemcpyAsync(T, tmp, sizeof(double) * sz * (nz + 1), cudaMemcpyDeviceToDevice, st);
+}
+
+cudaError_t build_pipe_spectrum(const GreenSpec& s, double* g64, float* g32, cudaStream_t st) {
+  const int nx = s.nx, ny = s.ny, nz = s.nz, M = s.modes_m, N = s.modes_n;
+  const long oct = long(nx + 1) * (ny + 1) * (nz + 1);
+  double *cx = nullptr, *cy = nullptr, *Z = nullptr, *U = nullptr, *T = nullptr, *tmp = nullptr,
+         *cosbuf = nullptr;
+  cudaError_t err = cudaSuccess;
+  const size_t szU = sizeof(double) * size_t(M) * (ny + 1) * (nz + 1);
+  if ((err = cudaMalloc(&cx, sizeof(double) * M * (nx + 1))) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&cy, sizeof(double) * N * (ny + 1))) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&Z, sizeof(double) * size_t(M) * N * (nz + 1))) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&U, szU)) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&T, sizeof(double) * oct)) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&tmp, sizeof(double) * oct)) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&cosbuf, sizeof(double) * 2 * (nz > nx ? (nz > ny ? nz : ny) : (nx > ny ? nx : ny))))
+      != cudaSuccess) goto done;
+  cos_table_kernel<<<nblk(M * (nx + 1), 256), 256, 0, st>>>(cx, M, nx, s.hx, s.a);
+  cos_table_kernel<<<nblk(N * (ny + 1), 256), 256, 0, st>>>(cy, N, ny, s.hy, s.b);
+  z_profile_kernel<<<nblk(long(M) * N * (nz + 1), 256), 256, 0, st>>>(Z, M, N, nz, s.hz, s.a, s.b,
+                                                                     s.igf);
+  contract_n_kernel<<<nblk(long(M) * (ny + 1) * (nz + 1), 256), 256, 0, st>>>(U, cy, Z, M, N, ny, nz);
+  contract_m_kernel<<<nblk(oct, 256), 256, 0, st>>>(T, cx, U, M, nx, ny, nz,
+                                                    2.0 * M_PI / (s.a * s.b));
+  if ((err = cudaGetLastError()) != cudaSuccess) goto done;
+  if ((err = octant_transform(T, tmp, cosbuf, nx, ny, nz, st)) != cudaSuccess) goto done;
+  finalize_kernel<<<nblk(oct, 256), 256, 0, st>>>(T, g64, g32, oct, s.scale);
+  if ((err = cudaGetLastError()) != cudaSuccess) goto done;
+  err = cudaStreamSynchronize(st);
+done:
+  cudaFree(cx); cudaFree(cy); cudaFree(Z); cudaFree(U); cudaFree(T); cudaFree(tmp); cudaFree(cosbuf);
+  return err;
+}
+
+cudaError_t build_free_spectrum(const GreenSpec& s, double self_value, double* g64, float* g32,
+                                cudaStream_t st) {
+  const int nx = s.nx, ny = s.ny, nz = s.nz;
+  const long oct = long(nx + 1) * (ny + 1) * (nz + 1);
+  double *T = nullptr, *tmp = nullptr, *cosbuf = nullptr;
+  cudaError_t err = cudaSuccess;
+  const int nmax = nz > nx ? (nz > ny ? nz : ny) : (nx > ny ? nx : ny);
+  if ((err = cudaMalloc(&T, sizeof(double) * oct)) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&tmp, sizeof(double) * oct)) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&cosbuf, sizeof(double) * 2 * nmax)) != cudaSuccess) goto done;
+  free_octant_kernel<<<nblk(oct, 256), 256, 0, st>>>(T, nx, ny, nz, s.hx, s.hy, s.hz, self_value);
+  if ((err = cudaGetLastError()) != cudaSuccess) goto done;
+  if ((err = octant_transform(T, tmp, cosbuf, nx, ny, nz, st)) != cudaSuccess) goto done;
+  finalize_kernel<<<nblk(oct, 256), 256, 0, st>>>(T, g64, g32, oct, s.scale);
+  if ((err = cudaGetLastError()) != cudaSuccess) goto done;
+  err = cudaStreamSynchronize(st);
+done:
+  cudaFree(T); cudaFree(tmp); cudaFree(cosbuf);
+  return err;
+}
+
+}  // namespace pp

@@ -1,0 +1,40 @@
+// Internal layout of pipe_handle (opaque in the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/pipe_poisson.h"
+
+namespace pp {
+// Kernel variant choices for one handle (filled by default_plan, refined by
+// pipe_autotune).
+struct Plan {
+  int z_warps;   // warps per CTA of the z transforms (8 or 16)
+};
+}  // namespace pp
+
+struct pipe_handle {
+  int device = 0;
+  pipe_geometry geom{};
+  pipe_grid grid{};
+  int kind = 0;          // 0 ordinary, 1 IGF, 2 free space
+  int sx = 0, sy = 0;    // correlation shifts 2*x0/hx, 2*y0/hy
+  int images = 1;        // four-term pipe operator (1) or free space (0)
+  double* green64 = nullptr;
+  float* green32 = nullptr;
+  void* work = nullptr;  // (nz+1)*nx*ny complex of the dtype
+  float2* tab32 = nullptr;
+  double2* tab64 = nullptr;
+  float2 *tw_t32 = nullptr, *w2_t32 = nullptr, *tw_z32 = nullptr, *w2_z32 = nullptr;
+  double2 *tw_t64 = nullptr, *w2_t64 = nullptr, *tw_z64 = nullptr, *w2_z64 = nullptr;
+  void* stage_rho = nullptr;   // device staging for pipe_poisson_solve_host
+  void* stage_phi = nullptr;
+  pp::Plan plan{8};
+  void* batch = nullptr;       // batched work list owned by this handle
+};
+
+namespace pp {
+Plan default_plan(int nz, bool f64);
+void batch_release(pipe_handle* h);
+int handle_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStream_t st);
+}  // namespace pp

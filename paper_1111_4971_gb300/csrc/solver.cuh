@@ -1,0 +1,83 @@
+// Shared declarations of the solve kernels (z transforms, transverse stage).
+#pragma once
+
+#include "fft_common.cuh"
+
+namespace pp {
+
+// Per-solve launch parameters (all device pointers).
+//   rho/phi : [nx][ny][nz] real, z contiguous
+//   work    : [nz+1][nx][ny] complex  (z half-spectrum, kz-plane major)
+//   green   : [nz+1][ny+1][nx+1] real octant of the scaled Green spectrum
+//   tw_t / w2_t : transverse group-FFT twiddles (length n) and w_{2n}^j, j<2n
+//   tw_z / w2_z : z group-FFT twiddles (length nz/2) and w_{2nz}^j, j<2nz
+template <typename T>
+struct SolveArgs {
+  const T* rho;
+  T* phi;
+  C2<T>* work;
+  const T* green;
+  const C2<T>* tw_t;
+  const C2<T>* w2_t;
+  const C2<T>* tw_z;
+  const C2<T>* w2_z;
+  int nx, ny, nz;
+  int sx, sy;        // correlation shifts 2*x0/hx, 2*y0/hy (integers)
+  int images;        // 1: four-term pipe operator, 0: free-space (one term)
+};
+
+// z transforms: one CTA handles COLS consecutive (i,j) columns.
+template <typename T, int NZ, int WARPS>
+struct ZCfg {
+  static constexpr int L = NZ / 2;                 // sub-FFT length
+  using S = GroupShape<L>;
+  static constexpr int G = S::G;
+  static constexpr int E = S::E;
+  static constexpr int UNIT = 2 * G;               // lanes per column (even + odd half)
+  static_assert(UNIT <= 32, "column unit must fit a warp");
+  static constexpr int CPW = 32 / UNIT;            // columns per warp
+  static constexpr int COLS = WARPS * CPW;         // columns per CTA
+  static constexpr int THREADS = 32 * WARPS;
+  // staging chunk: EC elements per lane -> 2*G*EC kz rows per chunk
+  static constexpr int EC = (E >= 4) ? 4 : E;
+  static constexpr int CH = 2 * G * EC;
+  static constexpr int SPAD = COLS + 1;            // padded staging row (complex)
+  static constexpr int GROUPS = THREADS / G;
+  // the FFT scratch tiles and the staging tile are live at different times
+  static constexpr size_t SCR = size_t(GROUPS) * S::SSTRIDE;
+  static constexpr size_t STG = size_t(CH + 1) * SPAD;
+  static constexpr size_t smem_bytes() { return sizeof(C2<T>) * (SCR > STG ? SCR : STG); }
+};
+
+template <typename T, int NZ, int WARPS, bool CONJ>
+__global__ void zfwd_kernel(SolveArgs<T> a);
+template <typename T, int NZ, int WARPS, bool CONJ>
+__global__ void zinv_kernel(SolveArgs<T> a);
+
+// transverse stage: one cluster of 2*H CTAs per kz plane.
+template <typename T, int N>
+struct TCfg {
+  using S = GroupShape<N>;
+  static constexpr int G = S::G;
+  static constexpr int E = S::E;
+  static constexpr int H = (sizeof(C2<T>) * N * N <= 140 * 1024) ? 1 : 2;   // row blocks
+  static constexpr int ROWS = N / H;
+  static constexpr int LD = ROWS + 1;            // padded column stride of the y-spectrum tile
+  static constexpr int THREADS = 256;
+  static constexpr int GROUPS = THREADS / G;
+  static constexpr int CLUSTER = 2 * H;
+  static constexpr size_t smem_bytes() {
+    return sizeof(C2<T>) * (size_t(N) * LD + size_t(GROUPS) * S::SSTRIDE);
+  }
+};
+
+template <typename T, int N, bool ADJ>
+__global__ void transverse_kernel(SolveArgs<T> a);
+
+// host launchers (defined next to the kernels)
+template <typename T>
+cudaError_t launch_z(bool forward, int warps, bool conj, const SolveArgs<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_transverse(bool adjoint, const SolveArgs<T>& a, cudaStream_t st);
+
+}  // namespace pp

@@ -1,0 +1,92 @@
+"""The C-ABI library loads and exports what include/pipe_poisson.h declares.
+
+CPU only: no call here launches a kernel (argument validation runs before any
+CUDA call).
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1111_4971_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pipe_poisson.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pipe_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1111_4971_gb300 import build
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported_and_bound(L):
+    names = declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIBPATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (pipe_[a-z0-9_]+)", out))
+    for n in names:
+        assert n in exported, n
+        assert n in _lib.SIGNATURES, n
+        assert getattr(L, n) is not None
+
+
+def test_compile_time_twiddles(L):
+    assert L.pipe_selftest_twiddles() <= 4.5e-16  # two ulp at 1.0
+
+
+def test_strerror_and_version(L):
+    assert L.pipe_strerror(0) == b"ok"
+    assert b"unsupported" in L.pipe_strerror(3)
+    assert b"sm_103a" in L.pipe_version()
+
+
+def _setup(L, geo, grid, igf=1):
+    h = ctypes.c_void_p()
+    st = L.pipe_green_setup(ctypes.byref(geo) if geo is not None else None,
+                            ctypes.byref(grid) if grid is not None else None, igf, ctypes.byref(h))
+    return st, h
+
+
+def test_setup_validation_without_gpu(L):
+    G, P = _lib.PipeGeometry, _lib.PipeGrid
+    good_geo = G(1.0, 1.0, 1 / 256, 1 / 256, 20, 20)
+    good = P(128, 128, 256, 1 / 128, 1 / 128, 0.1, 0)
+    cases = [
+        (None, good, 1, _lib.PIPE_EINVAL),
+        (good_geo, None, 1, _lib.PIPE_EINVAL),
+        (good_geo, good, 7, _lib.PIPE_EINVAL),                           # bad igf
+        (G(-1.0, 1.0, 0, 0, 20, 20), good, 1, _lib.PIPE_EINVAL),         # a <= 0
+        (good_geo, P(128, 128, 256, 0.0, 1 / 128, 0.1, 0), 1, _lib.PIPE_EINVAL),   # h = 0
+        (good_geo, P(128, 128, 256, 1 / 128, 1 / 128, 0.1, 5), 1, _lib.PIPE_EINVAL),  # dtype
+        (G(1.0, 1.0, 0.5, 0.0, 20, 20), good, 1, _lib.PIPE_EINVAL),      # mesh leaves the pipe
+        (G(1.0, 1.0, 0.0, 0.0, 0, 20), good, 1, _lib.PIPE_EINVAL),       # no modes
+        (good_geo, P(96, 96, 256, 1 / 96, 1 / 96, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),  # not 2^k
+        (good_geo, P(128, 64, 256, 1 / 128, 1 / 64, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),  # nx != ny
+        (good_geo, P(128, 128, 4096, 1 / 128, 1 / 128, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),
+        (G(2.0, 2.0, 0.5, 0.5, 20, 20), P(16, 16, 32, 0.1, 0.1, 0.1, 0), 1,
+         _lib.PIPE_EUNSUPPORTED),                                         # window, not spanning
+        (G(1.0, 1.0, 0.3 / 128, 0.5 / 128, 20, 20), good, 1, _lib.PIPE_EUNSUPPORTED),  # 2x0/h
+    ]
+    for geo, grid, igf, want in cases:
+        st, h = _setup(L, geo, grid, igf)
+        assert st == want, (geo, grid, igf, st)
+        assert not h.value
+
+
+def test_null_handle_and_pointers(L):
+    assert L.pipe_poisson_solve(None, None, None, None) == _lib.PIPE_EINVAL
+    assert L.pipe_poisson_adjoint(None, None, None, None) == _lib.PIPE_EINVAL
+    assert L.pipe_poisson_solve_host(None, None, None, None) == _lib.PIPE_EINVAL
+    assert L.pipe_green_spectrum(None, None, 0) == _lib.PIPE_EINVAL
+    L.pipe_green_destroy(None)
