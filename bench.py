@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the open-pipe Poisson solve on GB300.
+
+Workload: one 128x128x1024 IGF solve (padded 256x256x2048), a = b = 1,
+sigma_perp = 0.15, sigma_z = 3 (sigma_z/sigma_x = 20), Lz = 8 sigma_z, M = 20,
+FP32 path; a step is one full solve (z transform, transverse stage with the
+four-term Green product, inverse z transform) of a synthetic Gaussian bunch
+resident in HBM.  L2 (129 MB) is flushed by a 256 MB write between steps and
+the flush is outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the solve does not shard; N ranks run N independent replicas
+(weak scaling), value = total solves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pipe-Poisson solves/s at 128^2x1024 (FP32 vs FP64 at stated err); % HBM roofline"
+WORKLOAD = "pipe128x128x1024_igf"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling in the background during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(world, value):
+    import torch
+    if world == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_baseline(w, steps=1):
+    """The FP64 oracle (scipy.fft, literal four-term Eq. 10) on the host cores."""
+    import numpy as np
+    import scipy.fft
+    from oracle import pipe
+    cores = os.cpu_count() or 1
+    geom, grid, rho = w["geom"], w["grid"], w["rho"][0]
+    spectra = pipe.green_spectra(geom, grid, 1, workers=cores)     # setup, untimed
+    times = []
+    phi = None
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        phi = pipe.fft_solve(rho, geom, grid, 1, spectra=spectra, workers=cores)
+        times.append(time.perf_counter() - t0)
+    del spectra
+    return times, cores, phi
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle as it stands, timed per step."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from inputs import bunches
+    w = bunches.workload_throughput_128()
+    times, cores, _ = cpu_oracle_baseline(w, steps=args.warmup + args.steps)
+    timed = times[args.warmup:]
+    total = sum(timed)
+    value = len(timed) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [128, 128, 1024],
+                                        "padded": [256, 256, 2048], "green": "igf", "modes": 20},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": "one full 128x128x1024 solve per step (Green spectra "
+                                   "precomputed, untimed), scipy.fft with workers=cores"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from inputs import bunches
+    from paper_1111_4971_gb300 import PipeSolver
+
+    world, rank, local = dist_setup()
+    w = bunches.workload_throughput_128()
+    geom, grid, rho_np = w["geom"], w["grid"], w["rho"][0]
+    nx, ny, nz = grid.shape
+    dev = torch.device("cuda", local)
+
+    s32 = PipeSolver(geom, grid, igf=True, dtype=torch.float32)
+    if args.autotune:
+        s32.autotune()
+    rho = torch.tensor(rho_np, dtype=torch.float32, device=dev)
+    phi = s32.empty()
+    spec = s32.spectrum_buffer()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        s32.solve(rho, phi)
+    barrier(world)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    # ---- timed region: K solves ------------------------------------------
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        s32.solve(rho, phi)
+        ev[i][1].record(stream)
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall
+    solve_ms = [a.elapsed_time(b) for a, b in ev]
+    # ---- the same K steps through the stage entry points, per kernel -------
+    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e = kev[i]
+        e[0].record(stream)
+        s32.stage_z_forward(rho, spec)
+        e[1].record(stream)
+        s32.stage_transverse(spec)
+        e[2].record(stream)
+        s32.stage_z_inverse(spec, phi)
+        e[3].record(stream)
+    barrier(world)
+    clocks = sampler.stop()
+    k_ms = {
+        "z_forward": [e[0].elapsed_time(e[1]) for e in kev],
+        "transverse": [e[1].elapsed_time(e[2]) for e in kev],
+        "z_inverse": [e[2].elapsed_time(e[3]) for e in kev],
+    }
+    total_ms = max_over_ranks(world, sum(solve_ms))
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through host buffers (copies inside the call) ---------
+    rho_h = torch.tensor(rho_np, dtype=torch.float32).pin_memory()
+    phi_h = torch.empty((nx, ny, nz), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        s32.solve_host(rho_h, phi_h)
+    barrier(world)
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s32.solve_host(rho_h, phi_h)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = max_over_ranks(world, sum(e2e_ms))
+    e2e_value = world * args.steps / (e2e_total / 1e3)
+    nbytes = nx * ny * nz * 4
+
+    # ---- roofline of the dominant kernel ---------------------------------
+    peak, peak_kind = peaks()
+    means = {k: statistics.mean(v) for k, v in k_ms.items()}
+    dom = max(means, key=means.get)
+    plane = nx * ny * 8
+    green_plane = (nx + 1) * (ny + 1) * 4
+    alg_bytes = {
+        "z_forward": nx * ny * nz * 4 + (nz + 1) * plane,
+        "transverse": (nz + 1) * (2 * plane + green_plane),
+        "z_inverse": (nz + 1) * plane + nx * ny * nz * 4,
+    }
+    achieved = {k: alg_bytes[k] / (means[k] * 1e-3) / 1e9 for k in means}
+    b_pad = 4 * (2 * nx) * (2 * ny) * (nz + 1) * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [nx, ny, nz], "padded": [2 * nx, 2 * ny, 2 * nz],
+                   "green": "igf", "modes": 20, "sigma": [0.15, 0.15, 3.0],
+                   "parallelism": f"replicas{world}",
+                   "l2": "flushed between steps (256 MB write, outside the timed events)"},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved[dom], "peak": peak,
+                     "unit": "GB/s", "frac": achieved[dom] / peak, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes[dom], "kernel_ms": means[dom]},
+        "kernels_ms": means,
+        "kernels_gbs": achieved,
+        "b_pad": {"bytes": b_pad, "gbs": b_pad / (ms_per_step * 1e-3) / 1e9,
+                  "frac_of_measured": b_pad / (ms_per_step * 1e-3) / 1e9 / peak,
+                  "frac_of_8tbs": b_pad / (ms_per_step * 1e-3) / 1e9 / 8000.0},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "wall_s_timed_loop": t_wall,
+    }
+
+    # ---- FP64 path, free-space (Hockney) comparison, accuracy -------------
+    if rank == 0 and not args.quick:
+        s64 = PipeSolver(geom, grid, igf=True, dtype=torch.float64)
+        rho64 = torch.tensor(rho_np, dtype=torch.float64, device=dev)
+        phi64 = s64.empty()
+        for _ in range(2):
+            s64.solve(rho64, phi64)
+        t64 = []
+        for i in range(5):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s64.solve(rho64, phi64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t64.append(a.elapsed_time(b))
+        s32.solve(rho, phi)
+        torch.cuda.synchronize()
+        p32 = phi.double().cpu().numpy()
+        p64 = phi64.cpu().numpy()
+        err = float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))
+        sh = PipeSolver(None, grid, dtype=torch.float32, free_space=True)
+        phih = sh.empty()
+        for _ in range(2):
+            sh.solve(rho, phih)
+        th = []
+        for i in range(10):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sh.solve(rho, phih)
+            b.record(stream)
+            torch.cuda.synchronize()
+            th.append(a.elapsed_time(b))
+        line["fp64"] = {"solves_per_s": 1e3 / statistics.median(t64), "ms": statistics.median(t64)}
+        line["fp32_rel_l2_vs_fp64"] = err
+        line["hockney_fp32"] = {"solves_per_s": 1e3 / statistics.median(th), "ms": statistics.median(th)}
+        if args.check_oracle:
+            from oracle import pipe
+            nodes = [(64, 64, 512), (0, 0, 0), (127, 127, 1023), (5, 100, 300), (90, 30, 700)]
+            want = pipe.direct_sum_at(rho_np, geom, grid, 1, nodes)
+            got = np.array([p64[n] for n in nodes])
+            line["fp64_sampled_max_err_vs_direct_sum"] = float(np.abs(got - want).max()
+                                                               / np.abs(p64).max())
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times, cores, _ = cpu_oracle_baseline(w, steps=1)
+        line["cpu_baseline"] = {"value": 1.0 / times[0], "unit": "solves/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "one full 128x128x1024 FP64 solve of the same bunch "
+                                          "(scipy.fft four-term Eq. 10, Green spectra "
+                                          "precomputed and untimed)"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64 / Hockney extras")
+    ap.add_argument("--check-oracle", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

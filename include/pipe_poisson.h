@@ -159,6 +159,14 @@ int pipe_stage_z_inverse(pipe_handle* h, const void* spec, void* phi, int adjoin
  * appended to it. */
 int pipe_autotune(pipe_handle* h, void* stream);
 
+/* Read or pin the kernel variants a handle uses: z_warps in {8, 16} (CTA size of
+ * the z transforms), t_h in {1, 2} (the transverse cluster has 2*t_h CTAs, each
+ * holding nx/t_h rows of a kz plane), t_threads in {256, 512}.  pipe_set_plan
+ * returns PIPE_EINVAL for values outside those sets; a variant that does not
+ * fit the device (shared memory) makes the next solve fail with PIPE_ECUDA. */
+int pipe_get_plan(pipe_handle* h, int* z_warps, int* t_h, int* t_threads);
+int pipe_set_plan(pipe_handle* h, int z_warps, int t_h, int t_threads);
+
 /* Cloud-in-cell deposit of n macroparticles (positions xyz[n][3], FP64 or FP32
  * per the handle's dtype, charge q each) onto the handle's mesh nodes:
  * rho[i][j][k] += q * w / (hx*hy*hz), w the trilinear weight of node (i,j,k).

@@ -131,6 +131,18 @@ class PipeSolver:
 
     def autotune(self, stream=None):
         check(self.lib.pipe_autotune(self.handle, _stream_ptr(stream)), "pipe_autotune")
+        return self.plan
+
+    @property
+    def plan(self):
+        z, h, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self.lib.pipe_get_plan(self.handle, ctypes.byref(z), ctypes.byref(h), ctypes.byref(t)),
+              "pipe_get_plan")
+        return {"z_warps": z.value, "t_h": h.value, "t_threads": t.value}
+
+    def set_plan(self, z_warps, t_h, t_threads):
+        check(self.lib.pipe_set_plan(self.handle, int(z_warps), int(t_h), int(t_threads)),
+              "pipe_set_plan")
 
     def cic_deposit(self, xyz: torch.Tensor, charge: float, out: torch.Tensor | None = None,
                     stream=None):

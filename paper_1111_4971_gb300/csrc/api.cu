@@ -133,7 +133,8 @@ int run_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStre
   cudaError_t e;
   const int zw = h->plan.z_warps;
   if ((e = launch_z<T>(true, zw, adjoint, a, st)) != cudaSuccess) return status_of(e);
-  if ((e = launch_transverse<T>(adjoint, a, st)) != cudaSuccess) return status_of(e);
+  if ((e = launch_transverse<T>(adjoint, h->plan.t_h, h->plan.t_threads, a, st)) != cudaSuccess)
+    return status_of(e);
   if ((e = launch_z<T>(false, zw, adjoint, a, st)) != cudaSuccess) return status_of(e);
   return PIPE_OK;
 }
@@ -228,7 +229,7 @@ int pipe_green_setup(const pipe_geometry* geom, const pipe_grid* grid, int igf, 
   h->sx = sx;
   h->sy = sy;
   h->images = 1;
-  h->plan = default_plan(grid->nz, grid->dtype == PIPE_F64);
+  h->plan = default_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
   if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
   GreenSpec s;
   s.nx = grid->nx; s.ny = grid->ny; s.nz = grid->nz;
@@ -257,7 +258,7 @@ int pipe_free_space_setup(const pipe_grid* grid, double self_value, pipe_handle*
   h->kind = 2;
   h->sx = h->sy = 0;
   h->images = 0;
-  h->plan = default_plan(grid->nz, grid->dtype == PIPE_F64);
+  h->plan = default_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
   if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
   if (!(self_value > 0)) self_value = 1.0 / std::fmin(grid->hx, std::fmin(grid->hy, grid->hz));
   GreenSpec s;
@@ -341,9 +342,11 @@ int pipe_stage_transverse(pipe_handle* h, void* spec, int adjoint, void* stream)
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (h->grid.dtype == PIPE_F64)
-    e = launch_transverse<double>(adjoint != 0, make_args<double>(h, nullptr, nullptr, spec), s);
+    e = launch_transverse<double>(adjoint != 0, h->plan.t_h, h->plan.t_threads,
+                                  make_args<double>(h, nullptr, nullptr, spec), s);
   else
-    e = launch_transverse<float>(adjoint != 0, make_args<float>(h, nullptr, nullptr, spec), s);
+    e = launch_transverse<float>(adjoint != 0, h->plan.t_h, h->plan.t_threads,
+                                 make_args<float>(h, nullptr, nullptr, spec), s);
   return status_of(e);
 }
 

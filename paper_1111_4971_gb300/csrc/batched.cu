@@ -5,11 +5,6 @@
 #include "handle.cuh"
 
 namespace pp {
-Plan default_plan(int nz, bool f64) {
-  Plan p;
-  p.z_warps = (!f64 && nz >= 512) ? 16 : 8;
-  return p;
-}
 void batch_release(pipe_handle*) {}
 }  // namespace pp
 
@@ -18,4 +13,3 @@ extern "C" int pipe_poisson_solve_batched(pipe_handle* const*, const void* const
   return PIPE_EUNSUPPORTED;
 }
 extern "C" int pipe_batch_status(pipe_handle* const*, int) { return PIPE_OK; }
-extern "C" int pipe_autotune(pipe_handle*, void*) { return PIPE_OK; }

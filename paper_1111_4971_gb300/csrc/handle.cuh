@@ -9,7 +9,9 @@ namespace pp {
 // Kernel variant choices for one handle (filled by default_plan, refined by
 // pipe_autotune).
 struct Plan {
-  int z_warps;   // warps per CTA of the z transforms (8 or 16)
+  int z_warps;     // warps per CTA of the z transforms (8 or 16)
+  int t_h;         // row blocks of the transverse cluster (cluster = 2*t_h CTAs)
+  int t_threads;   // threads per transverse CTA (256 or 512)
 };
 }  // namespace pp
 
@@ -29,12 +31,12 @@ struct pipe_handle {
   double2 *tw_t64 = nullptr, *w2_t64 = nullptr, *tw_z64 = nullptr, *w2_z64 = nullptr;
   void* stage_rho = nullptr;   // device staging for pipe_poisson_solve_host
   void* stage_phi = nullptr;
-  pp::Plan plan{8};
+  pp::Plan plan{8, 1, 256};
   void* batch = nullptr;       // batched work list owned by this handle
 };
 
 namespace pp {
-Plan default_plan(int nz, bool f64);
+Plan default_plan(int n, int nz, bool f64);
 void batch_release(pipe_handle* h);
 int handle_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStream_t st);
 }  // namespace pp

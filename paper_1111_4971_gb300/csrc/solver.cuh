@@ -38,14 +38,12 @@ struct ZCfg {
   static constexpr int CPW = 32 / UNIT;            // columns per warp
   static constexpr int COLS = WARPS * CPW;         // columns per CTA
   static constexpr int THREADS = 32 * WARPS;
-  // staging chunk: EC elements per lane -> 2*G*EC kz rows per chunk
-  static constexpr int EC = (E >= 4) ? 4 : E;
-  static constexpr int CH = 2 * G * EC;
   static constexpr int SPAD = COLS + 1;            // padded staging row (complex)
   static constexpr int GROUPS = THREADS / G;
-  // the FFT scratch tiles and the staging tile are live at different times
+  // the FFT scratch tiles and the (nz+1) x COLS staging tile are live at
+  // different times and share the allocation
   static constexpr size_t SCR = size_t(GROUPS) * S::SSTRIDE;
-  static constexpr size_t STG = size_t(CH + 1) * SPAD;
+  static constexpr size_t STG = size_t(NZ + 1) * SPAD;
   static constexpr size_t smem_bytes() { return sizeof(C2<T>) * (SCR > STG ? SCR : STG); }
 };
 
@@ -54,30 +52,31 @@ __global__ void zfwd_kernel(SolveArgs<T> a);
 template <typename T, int NZ, int WARPS, bool CONJ>
 __global__ void zinv_kernel(SolveArgs<T> a);
 
-// transverse stage: one cluster of 2*H CTAs per kz plane.
-template <typename T, int N>
+// transverse stage: one cluster of 2*H CTAs per kz plane, THREADS per CTA.
+template <typename T, int N, int H_, int THREADS_>
 struct TCfg {
   using S = GroupShape<N>;
   static constexpr int G = S::G;
   static constexpr int E = S::E;
-  static constexpr int H = (sizeof(C2<T>) * N * N <= 140 * 1024) ? 1 : 2;   // row blocks
+  static constexpr int H = H_;                   // row blocks
   static constexpr int ROWS = N / H;
   static constexpr int LD = ROWS + 1;            // padded column stride of the y-spectrum tile
-  static constexpr int THREADS = 256;
+  static constexpr int THREADS = THREADS_;
   static constexpr int GROUPS = THREADS / G;
   static constexpr int CLUSTER = 2 * H;
   static constexpr size_t smem_bytes() {
     return sizeof(C2<T>) * (size_t(N) * LD + size_t(GROUPS) * S::SSTRIDE);
   }
 };
+constexpr size_t kMaxSmem = 227 * 1024;
 
-template <typename T, int N, bool ADJ>
+template <typename T, int N, int H, int THREADS, bool ADJ>
 __global__ void transverse_kernel(SolveArgs<T> a);
 
 // host launchers (defined next to the kernels)
 template <typename T>
 cudaError_t launch_z(bool forward, int warps, bool conj, const SolveArgs<T>& a, cudaStream_t st);
 template <typename T>
-cudaError_t launch_transverse(bool adjoint, const SolveArgs<T>& a, cudaStream_t st);
+cudaError_t launch_transverse(bool adjoint, int h, int threads, const SolveArgs<T>& a, cudaStream_t st);
 
 }  // namespace pp

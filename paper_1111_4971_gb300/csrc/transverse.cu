@@ -40,9 +40,9 @@ namespace cg = cooperative_groups;
 
 namespace pp {
 
-template <typename T, int N, bool ADJ>
-__global__ void __launch_bounds__(256) transverse_kernel(SolveArgs<T> a) {
-  using Cfg = TCfg<T, N>;
+template <typename T, int N, int H_, int THREADS_, bool ADJ>
+__global__ void __launch_bounds__(THREADS_) transverse_kernel(SolveArgs<T> a) {
+  using Cfg = TCfg<T, N, H_, THREADS_>;
   using V = C2<T>;
   constexpr int G = Cfg::G, E = Cfg::E, H = Cfg::H, ROWS = Cfg::ROWS, LD = Cfg::LD;
   constexpr int WARPS = Cfg::THREADS / 32;
@@ -230,56 +230,61 @@ __global__ void __launch_bounds__(256) transverse_kernel(SolveArgs<T> a) {
   cluster.sync();
 }
 
-template <typename T, int N, bool ADJ>
+template <typename T, int N, int H, int THREADS, bool ADJ>
 static cudaError_t tlaunch(const SolveArgs<T>& a, cudaStream_t st) {
-  using Cfg = TCfg<T, N>;
+  using Cfg = TCfg<T, N, H, THREADS>;
   const size_t smem = Cfg::smem_bytes();
-  void (*kern)(SolveArgs<T>) = transverse_kernel<T, N, ADJ>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
+  if constexpr (Cfg::smem_bytes() > kMaxSmem || (N / 2) / H < 1) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    void (*kern)(SolveArgs<T>) = transverse_kernel<T, N, H, THREADS, ADJ>;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(Cfg::CLUSTER * (a.nz + 1)), 1, 1);
+    cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = Cfg::CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(Cfg::CLUSTER * (a.nz + 1)), 1, 1);
-  cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = Cfg::CLUSTER;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 template <typename T, int N>
-static cudaError_t tlaunch2(bool adjoint, const SolveArgs<T>& a, cudaStream_t st) {
-  return adjoint ? tlaunch<T, N, true>(a, st) : tlaunch<T, N, false>(a, st);
+static cudaError_t tlaunch2(bool adjoint, int h, int threads, const SolveArgs<T>& a, cudaStream_t st) {
+#define PP_T_CASE(HH, TT)                                                           \
+  if (h == HH && threads == TT)                                                     \
+    return adjoint ? tlaunch<T, N, HH, TT, true>(a, st) : tlaunch<T, N, HH, TT, false>(a, st);
+  PP_T_CASE(1, 256)
+  PP_T_CASE(1, 512)
+  PP_T_CASE(2, 256)
+  PP_T_CASE(2, 512)
+#undef PP_T_CASE
+  return cudaErrorInvalidConfiguration;
 }
 
 #ifndef PP_T_TYPE
 #define PP_T_TYPE float
 #endif
-#define PP_T_INST(T, N)                                                   \
-  template __global__ void transverse_kernel<T, N, false>(SolveArgs<T>);  \
-  template __global__ void transverse_kernel<T, N, true>(SolveArgs<T>);
-PP_T_INST(PP_T_TYPE, 16)
-PP_T_INST(PP_T_TYPE, 32)
-PP_T_INST(PP_T_TYPE, 64)
-PP_T_INST(PP_T_TYPE, 128)
 
 template <>
-cudaError_t launch_transverse<PP_T_TYPE>(bool adjoint, const SolveArgs<PP_T_TYPE>& a,
-                                         cudaStream_t st) {
+cudaError_t launch_transverse<PP_T_TYPE>(bool adjoint, int h, int threads,
+                                         const SolveArgs<PP_T_TYPE>& a, cudaStream_t st) {
   using T = PP_T_TYPE;
   if (a.nx != a.ny) return cudaErrorInvalidValue;
   switch (a.nx) {
-    case 16: return tlaunch2<T, 16>(adjoint, a, st);
-    case 32: return tlaunch2<T, 32>(adjoint, a, st);
-    case 64: return tlaunch2<T, 64>(adjoint, a, st);
-    case 128: return tlaunch2<T, 128>(adjoint, a, st);
+    case 16: return tlaunch2<T, 16>(adjoint, h, threads, a, st);
+    case 32: return tlaunch2<T, 32>(adjoint, h, threads, a, st);
+    case 64: return tlaunch2<T, 64>(adjoint, h, threads, a, st);
+    case 128: return tlaunch2<T, 128>(adjoint, h, threads, a, st);
     default: return cudaErrorInvalidValue;
   }
 }

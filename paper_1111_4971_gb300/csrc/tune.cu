@@ -1,0 +1,182 @@
+// Kernel-variant plans and the autotuner.
+//
+// A plan picks, for one (n, nz, dtype) shape, the CTA size of the z
+// transforms and the cluster shape / CTA size of the transverse stage.  The
+// autotuner times every variant that fits the device with CUDA events on the
+// caller's stream and keeps the fastest; results are cached per shape for the
+// process and, if PIPE_TUNE_CACHE names a file, persisted there as lines
+// "n nz dtype z_warps t_h t_threads".
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "../../include/pipe_poisson.h"
+#include "handle.cuh"
+#include "solver.cuh"
+
+namespace pp {
+
+Plan default_plan(int n, int nz, bool f64) {
+  Plan p;
+  p.z_warps = (!f64 && nz >= 512) ? 16 : 8;
+  const size_t c = f64 ? 16 : 8;
+  p.t_h = (c * n * (n + 1) > 150 * 1024) ? 2 : 1;
+  p.t_threads = 256;
+  return p;
+}
+
+namespace {
+using Key = std::tuple<int, int, int>;
+std::mutex g_mu;
+std::map<Key, Plan>& cache() {
+  static std::map<Key, Plan> m;
+  return m;
+}
+
+void load_file_cache() {
+  static bool loaded = false;
+  if (loaded) return;
+  loaded = true;
+  const char* path = std::getenv("PIPE_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  int n, nz, dt, zw, th, tt;
+  while (std::fscanf(f, "%d %d %d %d %d %d", &n, &nz, &dt, &zw, &th, &tt) == 6)
+    cache()[Key(n, nz, dt)] = Plan{zw, th, tt};
+  std::fclose(f);
+}
+
+void save_file_cache(const Key& k, const Plan& p) {
+  const char* path = std::getenv("PIPE_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), p.z_warps,
+               p.t_h, p.t_threads);
+  std::fclose(f);
+}
+
+template <typename T>
+SolveArgs<T> args_for(pipe_handle* h, void* rho, void* phi);
+template <>
+SolveArgs<float> args_for<float>(pipe_handle* h, void* rho, void* phi) {
+  SolveArgs<float> a;
+  a.rho = static_cast<const float*>(rho); a.phi = static_cast<float*>(phi);
+  a.work = static_cast<float2*>(h->work); a.green = h->green32;
+  a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32;
+  a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
+  a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  return a;
+}
+template <>
+SolveArgs<double> args_for<double>(pipe_handle* h, void* rho, void* phi) {
+  SolveArgs<double> a;
+  a.rho = static_cast<const double*>(rho); a.phi = static_cast<double*>(phi);
+  a.work = static_cast<double2*>(h->work); a.green = h->green64;
+  a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64;
+  a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
+  a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  return a;
+}
+
+// mean time (ms) of `reps` runs of f on st, after 2 warm-ups; < 0 if f fails
+template <typename F>
+float time_ms(F&& f, cudaStream_t st, int reps) {
+  for (int i = 0; i < 2; ++i)
+    if (f() != cudaSuccess) { cudaGetLastError(); return -1.f; }
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, st);
+  for (int i = 0; i < reps; ++i) f();
+  cudaEventRecord(b, st);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+template <typename T>
+int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
+  const size_t n = size_t(h->grid.nx) * h->grid.ny * h->grid.nz;
+  void *rho = nullptr, *phi = nullptr;
+  if (cudaMalloc(&rho, n * sizeof(T)) != cudaSuccess) return PIPE_ENOMEM;
+  if (cudaMalloc(&phi, n * sizeof(T)) != cudaSuccess) { cudaFree(rho); return PIPE_ENOMEM; }
+  cudaMemsetAsync(rho, 0, n * sizeof(T), st);
+  SolveArgs<T> a = args_for<T>(h, rho, phi);
+  Plan best = h->plan;
+  float bz = 1e30f, bt = 1e30f;
+  const int reps = 5;
+  for (int zw : {8, 16}) {
+    float ms = time_ms([&] {
+      cudaError_t e = launch_z<T>(true, zw, false, a, st);
+      if (e != cudaSuccess) return e;
+      return launch_z<T>(false, zw, false, a, st);
+    }, st, reps);
+    if (ms > 0 && ms < bz) { bz = ms; best.z_warps = zw; }
+  }
+  const int shapes[4][2] = {{1, 256}, {1, 512}, {2, 256}, {2, 512}};
+  for (auto& sh : shapes) {
+    float ms = time_ms([&] { return launch_transverse<T>(false, sh[0], sh[1], a, st); }, st, reps);
+    if (ms > 0 && ms < bt) { bt = ms; best.t_h = sh[0]; best.t_threads = sh[1]; }
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(rho);
+  cudaFree(phi);
+  if (bz > 1e29f || bt > 1e29f) return PIPE_ECUDA;
+  *out = best;
+  return PIPE_OK;
+}
+}  // namespace
+
+}  // namespace pp
+
+using namespace pp;
+
+extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
+  if (!h) return PIPE_EINVAL;
+  const Key k(h->grid.nx, h->grid.nz, h->grid.dtype);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_file_cache();
+    auto it = cache().find(k);
+    if (it != cache().end()) { h->plan = it->second; return PIPE_OK; }
+  }
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) cudaSetDevice(h->device);
+  Plan p;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int s = h->grid.dtype == PIPE_F64 ? tune<double>(h, st, &p) : tune<float>(h, st, &p);
+  if (dev >= 0 && dev != h->device) cudaSetDevice(dev);
+  if (s != PIPE_OK) return s;
+  h->plan = p;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cache()[k] = p;
+  save_file_cache(k, p);
+  return PIPE_OK;
+}
+
+extern "C" int pipe_get_plan(pipe_handle* h, int* z_warps, int* t_h, int* t_threads) {
+  if (!h || !z_warps || !t_h || !t_threads) return PIPE_EINVAL;
+  *z_warps = h->plan.z_warps;
+  *t_h = h->plan.t_h;
+  *t_threads = h->plan.t_threads;
+  return PIPE_OK;
+}
+
+extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int t_h, int t_threads) {
+  if (!h) return PIPE_EINVAL;
+  if ((z_warps != 8 && z_warps != 16) || (t_h != 1 && t_h != 2) ||
+      (t_threads != 256 && t_threads != 512))
+    return PIPE_EINVAL;
+  h->plan = Plan{z_warps, t_h, t_threads};
+  return PIPE_OK;
+}

@@ -21,6 +21,19 @@
 
 namespace pp {
 
+// asynchronous global -> shared copy of one complex element (8 or 16 bytes)
+template <typename V>
+__device__ __forceinline__ void cp_async_elem(V* dst, const V* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  if constexpr (sizeof(V) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <typename T, int NZ, int WARPS, bool CONJ>
 __global__ void __launch_bounds__(32 * WARPS) zfwd_kernel(SolveArgs<T> a) {
   using Cfg = ZCfg<T, NZ, WARPS>;
@@ -67,27 +80,16 @@ __global__ void __launch_bounds__(32 * WARPS) zfwd_kernel(SolveArgs<T> a) {
   // X(nz) = Re Z(0) - Im Z(0), held by lane t=0 of the even half
   const V xN = mk<V>(z0.x - z0.y, T(0));
 
-  // staged, coalesced stores: chunk c covers kz in [c*CH, (c+1)*CH)
-  constexpr int NCH = E / Cfg::EC;
+  // staged, coalesced stores of the whole (nz+1) x COLS tile
+  __syncthreads();                                    // FFT scratch becomes the staging tile
 #pragma unroll
-  for (int c = 0; c < NCH; ++c) {
-    __syncthreads();
-#pragma unroll
-    for (int ee = 0; ee < Cfg::EC; ++ee) {
-      const int e = c * Cfg::EC + ee;
-      const int r = 2 * (t + G * ee) + p;               // row inside the chunk
-      stage[r * Cfg::SPAD + col_local] = v[e];
-    }
-    const bool last = (c == NCH - 1);
-    if (last && p == 0 && t == 0) stage[Cfg::CH * Cfg::SPAD + col_local] = CONJ ? cconj(xN) : xN;
-    __syncthreads();
-    const int rows = Cfg::CH + (last ? 1 : 0);
-    for (int idx = threadIdx.x; idx < rows * Cfg::COLS; idx += Cfg::THREADS) {
-      const int r = idx / Cfg::COLS;
-      const int cc = idx % Cfg::COLS;
-      if (col0 + cc < ncols)
-        a.work[size_t(c * Cfg::CH + r) * ncols + col0 + cc] = stage[r * Cfg::SPAD + cc];
-    }
+  for (int e = 0; e < E; ++e) stage[(2 * (t + G * e) + p) * Cfg::SPAD + col_local] = v[e];
+  if (p == 0 && t == 0) stage[NZ * Cfg::SPAD + col_local] = CONJ ? cconj(xN) : xN;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < (NZ + 1) * Cfg::COLS; idx += Cfg::THREADS) {
+    const int r = idx / Cfg::COLS;
+    const int cc = idx % Cfg::COLS;
+    if (col0 + cc < ncols) a.work[size_t(r) * ncols + col0 + cc] = stage[r * Cfg::SPAD + cc];
   }
 }
 
@@ -111,28 +113,18 @@ __global__ void __launch_bounds__(32 * WARPS) zinv_kernel(SolveArgs<T> a) {
   const bool valid = col < ncols;
   V* scratch = sbase + (threadIdx.x / G) * GroupShape<L>::SSTRIDE;
 
-  V v[E];
-  V xN = mk<V>(0, 0);
-  constexpr int NCH = E / Cfg::EC;
-#pragma unroll
-  for (int c = 0; c < NCH; ++c) {
-    const bool last = (c == NCH - 1);
-    const int rows = Cfg::CH + (last ? 1 : 0);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < rows * Cfg::COLS; idx += Cfg::THREADS) {
-      const int r = idx / Cfg::COLS;
-      const int cc = idx % Cfg::COLS;
-      stage[r * Cfg::SPAD + cc] = (col0 + cc < ncols)
-          ? a.work[size_t(c * Cfg::CH + r) * ncols + col0 + cc] : mk<V>(0, 0);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ee = 0; ee < Cfg::EC; ++ee) {
-      const int r = 2 * (t + G * ee) + p;
-      v[c * Cfg::EC + ee] = stage[r * Cfg::SPAD + col_local];
-    }
-    if (last) xN = stage[Cfg::CH * Cfg::SPAD + col_local];
+  // the whole (nz+1) x COLS tile in flight at once (cp.async, one element each)
+  for (int idx = threadIdx.x; idx < (NZ + 1) * Cfg::COLS; idx += Cfg::THREADS) {
+    const int r = idx / Cfg::COLS;
+    const int cc = idx % Cfg::COLS;
+    if (col0 + cc < ncols) cp_async_elem(&stage[r * Cfg::SPAD + cc], &a.work[size_t(r) * ncols + col0 + cc]);
   }
+  cp_async_wait_all();
+  __syncthreads();
+  V v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = stage[(2 * (t + G * e) + p) * Cfg::SPAD + col_local];
+  V xN = stage[NZ * Cfg::SPAD + col_local];
   __syncthreads();                                    // staging tile becomes FFT scratch
   if (CONJ) {
 #pragma unroll
@@ -177,6 +169,7 @@ template <typename T, int NZ, int W, bool C>
 static cudaError_t zlaunch(bool forward, const SolveArgs<T>& a, cudaStream_t st) {
   using Cfg = ZCfg<T, NZ, W>;
   const size_t smem = Cfg::smem_bytes();
+  if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
   void (*kern)(SolveArgs<T>) = forward ? zfwd_kernel<T, NZ, W, C> : zinv_kernel<T, NZ, W, C>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
