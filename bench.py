@@ -195,6 +195,13 @@ def run_ours(args):
     for _ in range(args.warmup):
         s32.solve(rho, phi)
     barrier(world)
+    if args.solves_only:                       # profiling target: K plain solves
+        for _ in range(args.steps):
+            s32.solve(rho, phi)
+        barrier(world)
+        if rank == 0:
+            print(json.dumps({"solves_only": args.steps, "plan": s32.plan}))
+        return 0
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -359,6 +366,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the FP64 / Hockney extras")
     ap.add_argument("--check-oracle", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--solves-only", action="store_true",
+                    help="setup, warm-up and K plain solves only (profiling target)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

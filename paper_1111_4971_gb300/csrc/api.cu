@@ -34,7 +34,9 @@ struct DeviceGuard {
   }
 };
 
+// lanes per FFT group, mirroring GroupShape (cyclic FFTs) and PairShape (paired)
 int sub_fft_group(int L) { return (L <= 32) ? 4 : (L <= 128 ? 8 : (L <= 512 ? 16 : 32)); }
+int pair_fft_group(int L) { return (L == 16) ? 2 : (L <= 64 ? 4 : (L <= 256 ? 8 : 16)); }
 
 // check that x is within rel of an integer; return it
 bool near_int(double x, int* out) {
@@ -77,16 +79,20 @@ int alloc_common(pipe_handle* h) {
   if ((e = cudaMalloc(&h->work, work)) != cudaSuccess) return status_of(e);
   const int n = g.nx, Lz = g.nz / 2;
   // float2 and double2 tables: tw_t (n), w2_t (2n), tw_z (nz/2), w2_z (2nz)
-  const size_t cnt = size_t(n) + 2 * n + Lz + 2 * g.nz;
+  const size_t cnt = size_t(n) + 2 * n + Lz + 2 * g.nz + 2 * n;
   if ((e = cudaMalloc(&h->tab32, cnt * sizeof(float2))) != cudaSuccess) return status_of(e);
   if ((e = cudaMalloc(&h->tab64, cnt * sizeof(double2))) != cudaSuccess) return status_of(e);
   h->tw_t32 = h->tab32; h->w2_t32 = h->tw_t32 + n; h->tw_z32 = h->w2_t32 + 2 * n; h->w2_z32 = h->tw_z32 + Lz;
+  h->tw_t2_32 = h->w2_z32 + 2 * g.nz;
   h->tw_t64 = h->tab64; h->w2_t64 = h->tw_t64 + n; h->tw_z64 = h->w2_t64 + 2 * n; h->w2_z64 = h->tw_z64 + Lz;
+  h->tw_t2_64 = h->w2_z64 + 2 * g.nz;
   cudaStream_t st = nullptr;
   launch_tables<float2>(h->tw_t32, h->w2_t32, n, sub_fft_group(n), 2 * n, st);
   launch_tables<float2>(h->tw_z32, h->w2_z32, Lz, sub_fft_group(Lz), 2 * g.nz, st);
   launch_tables<double2>(h->tw_t64, h->w2_t64, n, sub_fft_group(n), 2 * n, st);
   launch_tables<double2>(h->tw_z64, h->w2_z64, Lz, sub_fft_group(Lz), 2 * g.nz, st);
+  launch_tables<float2>(h->tw_t2_32, nullptr, 2 * n, pair_fft_group(2 * n), 0, st);
+  launch_tables<double2>(h->tw_t2_64, nullptr, 2 * n, pair_fft_group(2 * n), 0, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return status_of(e);
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return status_of(e);
   return PIPE_OK;
@@ -112,6 +118,7 @@ SolveArgs<float> make_args<float>(pipe_handle* h, const void* rho, void* phi, vo
   a.rho = static_cast<const float*>(rho); a.phi = static_cast<float*>(phi);
   a.work = static_cast<float2*>(work); a.green = h->green32;
   a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32;
+  a.tw_t2 = h->tw_t2_32;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
@@ -122,9 +129,16 @@ SolveArgs<double> make_args<double>(pipe_handle* h, const void* rho, void* phi, 
   a.rho = static_cast<const double*>(rho); a.phi = static_cast<double*>(phi);
   a.work = static_cast<double2*>(work); a.green = h->green64;
   a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64;
+  a.tw_t2 = h->tw_t2_64;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
+}
+
+template <typename T>
+cudaError_t transverse_stage(pipe_handle* h, bool adjoint, const SolveArgs<T>& a, cudaStream_t st) {
+  if (h->images) return launch_transverse_sym<T>(adjoint, h->plan.t_h, h->plan.t_threads, a, st);
+  return launch_transverse<T>(adjoint, h->free_plan.t_h, h->free_plan.t_threads, a, st);
 }
 
 template <typename T>
@@ -133,8 +147,7 @@ int run_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStre
   cudaError_t e;
   const int zw = h->plan.z_warps;
   if ((e = launch_z<T>(true, zw, adjoint, a, st)) != cudaSuccess) return status_of(e);
-  if ((e = launch_transverse<T>(adjoint, h->plan.t_h, h->plan.t_threads, a, st)) != cudaSuccess)
-    return status_of(e);
+  if ((e = transverse_stage<T>(h, adjoint, a, st)) != cudaSuccess) return status_of(e);
   if ((e = launch_z<T>(false, zw, adjoint, a, st)) != cudaSuccess) return status_of(e);
   return PIPE_OK;
 }
@@ -230,6 +243,7 @@ int pipe_green_setup(const pipe_geometry* geom, const pipe_grid* grid, int igf, 
   h->sy = sy;
   h->images = 1;
   h->plan = default_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
+  h->free_plan = default_free_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
   if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
   GreenSpec s;
   s.nx = grid->nx; s.ny = grid->ny; s.nz = grid->nz;
@@ -259,6 +273,7 @@ int pipe_free_space_setup(const pipe_grid* grid, double self_value, pipe_handle*
   h->sx = h->sy = 0;
   h->images = 0;
   h->plan = default_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
+  h->free_plan = default_free_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
   if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
   if (!(self_value > 0)) self_value = 1.0 / std::fmin(grid->hx, std::fmin(grid->hy, grid->hz));
   GreenSpec s;
@@ -342,11 +357,9 @@ int pipe_stage_transverse(pipe_handle* h, void* spec, int adjoint, void* stream)
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (h->grid.dtype == PIPE_F64)
-    e = launch_transverse<double>(adjoint != 0, h->plan.t_h, h->plan.t_threads,
-                                  make_args<double>(h, nullptr, nullptr, spec), s);
+    e = transverse_stage<double>(h, adjoint != 0, make_args<double>(h, nullptr, nullptr, spec), s);
   else
-    e = launch_transverse<float>(adjoint != 0, h->plan.t_h, h->plan.t_threads,
-                                 make_args<float>(h, nullptr, nullptr, spec), s);
+    e = transverse_stage<float>(h, adjoint != 0, make_args<float>(h, nullptr, nullptr, spec), s);
   return status_of(e);
 }
 

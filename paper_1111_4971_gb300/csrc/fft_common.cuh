@@ -138,9 +138,9 @@ __device__ __forceinline__ void static_for(F&& f) {
 }
 
 // ---------------------------------------------------------------------------
-// In-register DFT of N points with stride S inside an array: x[OFF + S*n].
-// Natural order in, natural order out.  Radix-2 decimation in time with a
-// radix-4 leaf; every index and twiddle is a compile-time constant.
+// In-register DFT of N points on x[0..N-1], natural order in and out.
+// Radix-4 decimation in time (radix-2 for an odd power of two at the top);
+// every index and twiddle is a compile-time constant.
 // ---------------------------------------------------------------------------
 template <int N, bool INV, typename V>
 __device__ __forceinline__ void dft_reg(V* x) {
@@ -158,7 +158,29 @@ __device__ __forceinline__ void dft_reg(V* x) {
     x[2] = csub(s0, s1);
     x[1] = cadd(d0, d1r);
     x[3] = csub(d0, d1r);
-  } else {
+  } else if constexpr ((N & 0x55555555) != 0) {      // N = 4^k: radix 4
+    constexpr int Q = N / 4;
+    V a[4][Q];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a[r][i] = x[4 * i + r];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) dft_reg<Q, INV>(a[r]);
+    static_for<0, Q>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      V y0 = a[0][k];
+      V y1 = twiddle_const<N, k, INV>(a[1][k]);
+      V y2 = twiddle_const<N, 2 * k, INV>(a[2][k]);
+      V y3 = twiddle_const<N, 3 * k, INV>(a[3][k]);
+      V s0 = cadd(y0, y2), d0 = csub(y0, y2);
+      V s1 = cadd(y1, y3), d1 = twiddle_const<4, 1, INV>(csub(y1, y3));
+      x[k] = cadd(s0, s1);
+      x[k + 2 * Q] = csub(s0, s1);
+      x[k + Q] = cadd(d0, d1);
+      x[k + 3 * Q] = csub(d0, d1);
+    });
+  } else {                                             // N = 2 * 4^k: one radix-2 step
     constexpr int H = N / 2;
     V e[H], o[H];
 #pragma unroll
@@ -175,6 +197,161 @@ __device__ __forceinline__ void dft_reg(V* x) {
       x[k + H] = csub(e[k], t);
     });
   }
+}
+
+// ---------------------------------------------------------------------------
+// Group FFTs with the "paired" spectral layout.
+//
+// L = E x G; a group of G lanes, lane t.  Time-domain data use the cyclic
+// layout (lane t holds n = t + G*e).  Spectral data use the paired layout:
+// lane t owns U = E/(2G) pairs of rows k1 of the E x G index grid
+// q = k1 + E*k2, and for each owned row all G values k2, in
+// v[(2j+s)*G + k2] (pair j, member s).  Rows are paired so that the mirror
+// frequency of every element the lane holds is held by the same lane:
+//   EVEN pairing (mirror q -> -q mod L):    rows {u, E-u}, u = t + G j; u = 0 -> {0, E/2}
+//   ODD  pairing (mirror q -> L-1-q):       rows {u, E-1-u}
+// ODD also selects the odd frequencies of the 2L-point transform of the
+// zero-padded sequence: X(q) = sum_n x_n w_{2L}^{n(2q+1)}.  Its twist is
+// split into a compile-time factor w_{2E}^{e} and a twiddle table
+// tw_odd[k1][t] = w_{2L}^{t(2k1+1)}; the even table is tw_even[k1][t] = w_L^{t k1}.
+// ---------------------------------------------------------------------------
+template <int L> struct PairShape {
+  static_assert(L >= 16 && L <= 512 && (L & (L - 1)) == 0, "FFT length");
+  static constexpr int G = (L == 16) ? 2 : (L <= 64 ? 4 : (L <= 256 ? 8 : 16));
+  static constexpr int E = L / G;
+  static constexpr int U = E / (2 * G);               // row pairs per lane
+  static_assert(U >= 1 && E % (2 * G) == 0, "paired shape");
+  // padded scratch tile, complex elements per group; groups are spaced by
+  // SSTRIDE so that two groups of one half-warp fall on different banks
+  static constexpr int SCRATCH = E * (G + 1);
+  static constexpr int SSTRIDE = SCRATCH + 8;
+};
+
+// row of member s of pair j held by lane t
+template <int L, bool ODDP>
+__device__ __forceinline__ int pair_row(int t, int j, int s) {
+  constexpr int G = PairShape<L>::G, E = PairShape<L>::E;
+  const int u = t + G * j;
+  if constexpr (ODDP) {
+    return s ? (E - 1 - u) : u;
+  } else {
+    if (u == 0) return s ? E / 2 : 0;
+    return s ? (E - u) : u;
+  }
+}
+
+// frequency index q of slot idx = (2j+s)*G + k2
+template <int L, bool ODDP>
+__device__ __forceinline__ int paired_q(int t, int idx) {
+  constexpr int G = PairShape<L>::G, E = PairShape<L>::E;
+  return pair_row<L, ODDP>(t, idx / (2 * G), (idx / G) & 1) + E * (idx % G);
+}
+
+// slot of the mirror of slot idx (compile-time idx): general rule, and the
+// rule of the self-paired unit u = 0 of the EVEN pairing (lane 0, pair 0)
+template <int L, int IDX>
+struct MirrorSlot {
+  static constexpr int G = PairShape<L>::G;
+  static constexpr int j = IDX / (2 * G), s = (IDX / G) & 1, k2 = IDX % G;
+  static constexpr int general = (2 * j + (1 - s)) * G + (G - 1 - k2);
+  static constexpr int unit0 = (s == 0) ? (2 * j) * G + ((G - k2) % G) : (2 * j + 1) * G + (G - 1 - k2);
+};
+
+// cyclic time layout -> paired spectral layout.  tw: tw_even or tw_odd per ODDP.
+template <int L, bool INV, bool ODDP, typename V>
+__device__ __forceinline__ void fft_c2p(V (&v)[PairShape<L>::E], V* scratch, const V* tw, int t) {
+  constexpr int G = PairShape<L>::G, E = PairShape<L>::E, U = PairShape<L>::U;
+  if constexpr (ODDP) {
+    static_for<1, E>([&](auto ec) {
+      constexpr int e = decltype(ec)::value;
+      v[e] = twiddle_const<2 * E, e, INV>(v[e]);
+    });
+  }
+  dft_reg<E, INV>(v);
+#pragma unroll
+  for (int k1 = (ODDP ? 0 : 1); k1 < E; ++k1) v[k1] = cmulc<INV>(v[k1], tw[k1 * G + t]);
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < E; ++k1) scratch[k1 * (G + 1) + t] = v[k1];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int r = pair_row<L, ODDP>(t, j, s);
+      V u[G];
+#pragma unroll
+      for (int tt = 0; tt < G; ++tt) u[tt] = scratch[r * (G + 1) + tt];
+      dft_reg<G, INV>(u);
+#pragma unroll
+      for (int k2 = 0; k2 < G; ++k2) v[(2 * j + s) * G + k2] = u[k2];
+    }
+  }
+}
+
+// paired spectral layout -> cyclic time layout (the transpose of fft_c2p's
+// index map): y_n = sum_q X(q) w_L^{qn}, times w_{2L}^{n} when ODDP.
+template <int L, bool INV, bool ODDP, typename V>
+__device__ __forceinline__ void fft_p2c(V (&v)[PairShape<L>::E], V* scratch, const V* tw, int t) {
+  constexpr int G = PairShape<L>::G, E = PairShape<L>::E, U = PairShape<L>::U;
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      dft_reg<G, INV>(&v[(2 * j + s) * G]);
+      const int r = pair_row<L, ODDP>(t, j, s);
+#pragma unroll
+      for (int n2 = 1; n2 < G; ++n2)          // column n2 = 0 of both tables is 1
+        v[(2 * j + s) * G + n2] = cmulc<INV>(v[(2 * j + s) * G + n2], tw[r * G + n2]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < U; ++j)
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int r = pair_row<L, ODDP>(t, j, s);
+#pragma unroll
+      for (int n2 = 0; n2 < G; ++n2) scratch[r * (G + 1) + n2] = v[(2 * j + s) * G + n2];
+    }
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < E; ++k1) v[k1] = scratch[k1 * (G + 1) + t];
+  dft_reg<E, INV>(v);
+  if constexpr (ODDP) {
+    static_for<1, E>([&](auto nc) {
+      constexpr int n1 = decltype(nc)::value;
+      v[n1] = twiddle_const<2 * E, n1, INV>(v[n1]);
+    });
+  }
+}
+
+// v[idx] <- f(v[idx], v[mirror(idx)], idx) for every slot, EVEN pairing, in
+// lane (the mirror of frequency q is -q mod L).  Pairs never cross the first
+// 2G slots, so those go through a small copy (the self-paired unit of lane 0
+// pairs them differently) and the rest are updated pairwise in place.
+template <int L, typename V, typename F>
+__device__ __forceinline__ void apply_mirror_pairs(V (&v)[PairShape<L>::E], int t, F&& f) {
+  constexpr int G = PairShape<L>::G, E = PairShape<L>::E;
+  const bool u0 = (t == 0);
+  V mm[2 * G];
+  static_for<0, 2 * G>([&](auto ic) {
+    constexpr int idx = decltype(ic)::value;
+    mm[idx] = u0 ? v[MirrorSlot<L, idx>::unit0] : v[MirrorSlot<L, idx>::general];
+  });
+  static_for<2 * G, E>([&](auto ic) {
+    constexpr int idx = decltype(ic)::value;
+    constexpr int g = MirrorSlot<L, idx>::general;
+    if constexpr (idx < g) {
+      const V a = v[idx], b = v[g];
+      v[idx] = f(a, b, idx);
+      v[g] = f(b, a, g);
+    }
+  });
+  static_for<0, 2 * G>([&](auto ic) {
+    constexpr int idx = decltype(ic)::value;
+    v[idx] = f(v[idx], mm[idx], idx);
+  });
 }
 
 // ---------------------------------------------------------------------------

@@ -10,8 +10,8 @@ namespace pp {
 // pipe_autotune).
 struct Plan {
   int z_warps;     // warps per CTA of the z transforms (8 or 16)
-  int t_h;         // row blocks of the transverse cluster (cluster = 2*t_h CTAs)
-  int t_threads;   // threads per transverse CTA (256 or 512)
+  int t_h;         // transverse stage: row blocks per kz plane (CTAs per cluster)
+  int t_threads;   // threads per transverse CTA
 };
 }  // namespace pp
 
@@ -27,16 +27,18 @@ struct pipe_handle {
   void* work = nullptr;  // (nz+1)*nx*ny complex of the dtype
   float2* tab32 = nullptr;
   double2* tab64 = nullptr;
-  float2 *tw_t32 = nullptr, *w2_t32 = nullptr, *tw_z32 = nullptr, *w2_z32 = nullptr;
-  double2 *tw_t64 = nullptr, *w2_t64 = nullptr, *tw_z64 = nullptr, *w2_z64 = nullptr;
+  float2 *tw_t32 = nullptr, *w2_t32 = nullptr, *tw_z32 = nullptr, *w2_z32 = nullptr, *tw_t2_32 = nullptr;
+  double2 *tw_t64 = nullptr, *w2_t64 = nullptr, *tw_z64 = nullptr, *w2_z64 = nullptr, *tw_t2_64 = nullptr;
   void* stage_rho = nullptr;   // device staging for pipe_poisson_solve_host
   void* stage_phi = nullptr;
   pp::Plan plan{8, 1, 256};
+  pp::Plan free_plan{8, 1, 256};   // transverse shape of the free-space stage
   void* batch = nullptr;       // batched work list owned by this handle
 };
 
 namespace pp {
-Plan default_plan(int n, int nz, bool f64);
+Plan default_plan(int n, int nz, bool f64);        // pipe operator
+Plan default_free_plan(int n, int nz, bool f64);   // free-space stage
 void batch_release(pipe_handle* h);
 int handle_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStream_t st);
 }  // namespace pp

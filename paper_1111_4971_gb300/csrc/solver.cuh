@@ -19,6 +19,7 @@ struct SolveArgs {
   const T* green;
   const C2<T>* tw_t;
   const C2<T>* w2_t;
+  const C2<T>* tw_t2;   // paired-layout twiddles of the 2n-point transverse FFTs
   const C2<T>* tw_z;
   const C2<T>* w2_z;
   int nx, ny, nz;
@@ -70,6 +71,26 @@ struct TCfg {
 };
 constexpr size_t kMaxSmem = 227 * 1024;
 
+// transverse stage of the pipe operator (full-span meshes): one cluster of HB
+// CTAs per kz plane; CTA h holds rows [h*N/HB, (h+1)*N/HB) of u[ky = 1..N][i].
+// The tile is unpadded with the row index XOR-swizzled by the column
+// (conflict-free row and column accesses).
+template <typename T, int N, int HB, int THREADS>
+struct TSymCfg {
+  static constexpr int L = 2 * N;
+  using S = PairShape<L>;
+  static constexpr int G = S::G;
+  static constexpr int E = S::E;
+  static constexpr int ROWS = N / HB;
+  static constexpr int LD = ROWS;
+  static constexpr int SWM = (ROWS < 16 ? ROWS : 16) - 1;
+  static constexpr int YBUF = N * LD;
+  static constexpr int GROUPS = THREADS / G;
+  static constexpr size_t smem_bytes() {
+    return sizeof(C2<T>) * (size_t(YBUF) + 2 * size_t(L) + size_t(GROUPS) * S::SSTRIDE);
+  }
+};
+
 template <typename T, int N, int H, int THREADS, bool ADJ>
 __global__ void transverse_kernel(SolveArgs<T> a);
 
@@ -78,5 +99,8 @@ template <typename T>
 cudaError_t launch_z(bool forward, int warps, bool conj, const SolveArgs<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_transverse(bool adjoint, int h, int threads, const SolveArgs<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_transverse_sym(bool adjoint, int hb, int threads, const SolveArgs<T>& a,
+                                  cudaStream_t st);
 
 }  // namespace pp

@@ -23,8 +23,17 @@ namespace pp {
 Plan default_plan(int n, int nz, bool f64) {
   Plan p;
   p.z_warps = (!f64 && nz >= 512) ? 16 : 8;
+  if (n < 128) { p.t_h = 1; p.t_threads = 256; }
+  else if (!f64) { p.t_h = 2; p.t_threads = 256; }
+  else { p.t_h = 4; p.t_threads = 128; }
+  return p;
+}
+
+Plan default_free_plan(int n, int nz, bool f64) {
+  Plan p;
+  p.z_warps = (!f64 && nz >= 512) ? 16 : 8;
   const size_t c = f64 ? 16 : 8;
-  p.t_h = (c * n * (n + 1) > 150 * 1024) ? 2 : 1;
+  p.t_h = (n >= 128 || c * n * (n + 1) > 150 * 1024) ? 2 : 1;
   p.t_threads = 256;
   return p;
 }
@@ -69,6 +78,7 @@ SolveArgs<float> args_for<float>(pipe_handle* h, void* rho, void* phi) {
   a.rho = static_cast<const float*>(rho); a.phi = static_cast<float*>(phi);
   a.work = static_cast<float2*>(h->work); a.green = h->green32;
   a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32;
+  a.tw_t2 = h->tw_t2_32;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
@@ -79,6 +89,7 @@ SolveArgs<double> args_for<double>(pipe_handle* h, void* rho, void* phi) {
   a.rho = static_cast<const double*>(rho); a.phi = static_cast<double*>(phi);
   a.work = static_cast<double2*>(h->work); a.green = h->green64;
   a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64;
+  a.tw_t2 = h->tw_t2_64;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
@@ -111,7 +122,7 @@ int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
   if (cudaMalloc(&phi, n * sizeof(T)) != cudaSuccess) { cudaFree(rho); return PIPE_ENOMEM; }
   cudaMemsetAsync(rho, 0, n * sizeof(T), st);
   SolveArgs<T> a = args_for<T>(h, rho, phi);
-  Plan best = h->plan;
+  Plan best = h->images ? h->plan : h->free_plan;
   float bz = 1e30f, bt = 1e30f;
   const int reps = 5;
   for (int zw : {8, 16}) {
@@ -122,10 +133,18 @@ int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
     }, st, reps);
     if (ms > 0 && ms < bz) { bz = ms; best.z_warps = zw; }
   }
-  const int shapes[4][2] = {{1, 256}, {1, 512}, {2, 256}, {2, 512}};
-  for (auto& sh : shapes) {
-    float ms = time_ms([&] { return launch_transverse<T>(false, sh[0], sh[1], a, st); }, st, reps);
-    if (ms > 0 && ms < bt) { bt = ms; best.t_h = sh[0]; best.t_threads = sh[1]; }
+  if (h->images) {
+    const int shapes[6][2] = {{1, 128}, {1, 256}, {2, 128}, {2, 256}, {4, 128}, {4, 256}};
+    for (auto& sh : shapes) {
+      float ms = time_ms([&] { return launch_transverse_sym<T>(false, sh[0], sh[1], a, st); }, st, reps);
+      if (ms > 0 && ms < bt) { bt = ms; best.t_h = sh[0]; best.t_threads = sh[1]; }
+    }
+  } else {
+    const int shapes[4][2] = {{1, 256}, {1, 512}, {2, 256}, {2, 512}};
+    for (auto& sh : shapes) {
+      float ms = time_ms([&] { return launch_transverse<T>(false, sh[0], sh[1], a, st); }, st, reps);
+      if (ms > 0 && ms < bt) { bt = ms; best.t_h = sh[0]; best.t_threads = sh[1]; }
+    }
   }
   cudaStreamSynchronize(st);
   cudaFree(rho);
@@ -142,12 +161,16 @@ using namespace pp;
 
 extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
   if (!h) return PIPE_EINVAL;
-  const Key k(h->grid.nx, h->grid.nz, h->grid.dtype);
+  const Key k(h->grid.nx, h->grid.nz, h->grid.dtype + (h->images ? 0 : 2));
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_file_cache();
     auto it = cache().find(k);
-    if (it != cache().end()) { h->plan = it->second; return PIPE_OK; }
+    if (it != cache().end()) {
+      if (h->images) h->plan = it->second;
+      else { h->plan.z_warps = it->second.z_warps; h->free_plan = it->second; }
+      return PIPE_OK;
+    }
   }
   int dev = -1;
   cudaGetDevice(&dev);
@@ -157,7 +180,8 @@ extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
   const int s = h->grid.dtype == PIPE_F64 ? tune<double>(h, st, &p) : tune<float>(h, st, &p);
   if (dev >= 0 && dev != h->device) cudaSetDevice(dev);
   if (s != PIPE_OK) return s;
-  h->plan = p;
+  if (h->images) h->plan = p;
+  else { h->plan.z_warps = p.z_warps; h->free_plan = p; }
   std::lock_guard<std::mutex> lk(g_mu);
   cache()[k] = p;
   save_file_cache(k, p);
@@ -166,17 +190,19 @@ extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
 
 extern "C" int pipe_get_plan(pipe_handle* h, int* z_warps, int* t_h, int* t_threads) {
   if (!h || !z_warps || !t_h || !t_threads) return PIPE_EINVAL;
+  const Plan& p = h->images ? h->plan : h->free_plan;
   *z_warps = h->plan.z_warps;
-  *t_h = h->plan.t_h;
-  *t_threads = h->plan.t_threads;
+  *t_h = p.t_h;
+  *t_threads = p.t_threads;
   return PIPE_OK;
 }
 
 extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int t_h, int t_threads) {
   if (!h) return PIPE_EINVAL;
-  if ((z_warps != 8 && z_warps != 16) || (t_h != 1 && t_h != 2) ||
-      (t_threads != 256 && t_threads != 512))
+  if ((z_warps != 8 && z_warps != 16) || (t_h != 1 && t_h != 2 && t_h != 4) ||
+      (t_threads != 128 && t_threads != 256 && t_threads != 512))
     return PIPE_EINVAL;
-  h->plan = Plan{z_warps, t_h, t_threads};
+  if (h->images) h->plan = Plan{z_warps, t_h, t_threads};
+  else { h->plan.z_warps = z_warps; h->free_plan = Plan{z_warps, t_h, t_threads}; }
   return PIPE_OK;
 }
