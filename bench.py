@@ -170,6 +170,53 @@ def run_reference(args):
     return 0
 
 
+def bench_batched(args, count=96):
+    """96 independent IGF solves on mixed grids / aspect ratios: one persistent
+    launch replayed from a CUDA graph, against a loop of single solves."""
+    import torch
+
+    from inputs import bunches
+    from paper_1111_4971_gb300 import PipeSolver, batch_status, solve_batched
+    items = bunches.workload_batched_96(count=count)
+    solvers, rhos = [], []
+    for it in items:
+        s = PipeSolver(it["geom"], it["grid"], igf=True, dtype=torch.float32)
+        solvers.append(s)
+        rhos.append(torch.tensor(it["rho"], dtype=torch.float32, device="cuda"))
+    phis = [s.empty() for s in solvers]
+    grids = sorted({(it["grid"].nx, it["grid"].nz) for it in items})
+    for s in solvers:                   # autotuned plans for the loop of single solves
+        s.autotune()
+    stream = torch.cuda.Stream()
+    reps = max(5, args.steps // 4)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    with torch.cuda.stream(stream):
+        loop_ms = timed(lambda: [s.solve(r, p, stream=stream) for s, r, p in zip(solvers, rhos, phis)])
+        solve_batched(solvers, rhos, phis, stream=stream)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            solve_batched(solvers, rhos, phis, stream=stream)
+        batch_ms = timed(g.replay)
+    ok = batch_status(solvers) == 0
+    return {"solves": count, "grids": grids, "batched_ms": batch_ms, "loop_ms": loop_ms,
+            "batched_solves_per_s": count / (batch_ms * 1e-3),
+            "loop_solves_per_s": count / (loop_ms * 1e-3), "speedup": loop_ms / batch_ms,
+            "status_ok": ok, "launches_per_batch": 1}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -340,6 +387,9 @@ def run_ours(args):
             got = np.array([p64[n] for n in nodes])
             line["fp64_sampled_max_err_vs_direct_sum"] = float(np.abs(got - want).max()
                                                                / np.abs(p64).max())
+
+    if rank == 0 and not args.quick:
+        line["batched"] = bench_batched(args)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times, cores, _ = cpu_oracle_baseline(w, steps=1)

@@ -133,6 +133,15 @@ int pipe_poisson_solve_batched(pipe_handle* const* handles, const void* const* r
  * batch plan: PIPE_OK or PIPE_ETIMEOUT.  Synchronous (copies one word). */
 int pipe_batch_status(pipe_handle* const* handles, int n);
 
+/* Failure-detection test hook for the batched launch: the NEXT
+ * pipe_poisson_solve_batched call with this exact handle set (whose work list
+ * must already exist, i.e. after one normal call) skips every item of stage
+ * `drop_stage` (0 z-forward, 1 transverse, 2 z-inverse) without counting it
+ * and polls at most `spin_limit` times per wait, so the dependent waits give
+ * up and the batch status becomes PIPE_ETIMEOUT while the kernel still ends.
+ * The results of that call are undefined.  Errors: PIPE_EINVAL. */
+int pipe_batch_inject_fault(pipe_handle* const* handles, int n, int drop_stage, long long spin_limit);
+
 /* Copy the handle's FP64 Green spectrum (the real octant g[kz][ky][kx],
  * kz <= nz, ky <= ny, kx <= nx, already multiplied by hx*hy*hz/(8*nx*ny*nz))
  * to host memory `out` of `count` doubles; count must equal
@@ -160,12 +169,14 @@ int pipe_stage_z_inverse(pipe_handle* h, const void* spec, void* phi, int adjoin
 int pipe_autotune(pipe_handle* h, void* stream);
 
 /* Read or pin the kernel variants a handle uses: z_warps in {8, 16} (CTA size of
- * the z transforms), t_h in {1, 2} (the transverse cluster has 2*t_h CTAs, each
- * holding nx/t_h rows of a kz plane), t_threads in {256, 512}.  pipe_set_plan
- * returns PIPE_EINVAL for values outside those sets; a variant that does not
- * fit the device (shared memory) makes the next solve fail with PIPE_ECUDA. */
-int pipe_get_plan(pipe_handle* h, int* z_warps, int* t_h, int* t_threads);
-int pipe_set_plan(pipe_handle* h, int z_warps, int t_h, int t_threads);
+ * the z transforms), z_pipe in {0, 1} (1: each z CTA walks several tiles and
+ * streams the next tile's input while transforming the current one), t_h in
+ * {1, 2, 4} (the transverse stage runs t_h CTAs per kz plane, each holding
+ * nx/t_h rows), t_threads in {128, 256, 512}.  pipe_set_plan returns
+ * PIPE_EINVAL for values outside those sets; a variant that does not fit the
+ * device (shared memory) makes the next solve fail with PIPE_ECUDA. */
+int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h, int* t_threads);
+int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads);
 
 /* Cloud-in-cell deposit of n macroparticles (positions xyz[n][3], FP64 or FP32
  * per the handle's dtype, charge q each) onto the handle's mesh nodes:

@@ -18,8 +18,8 @@ import torch
 from . import _lib
 from ._lib import PipeError, PipeGeometry, PipeGrid, check
 
-__all__ = ["PipeSolver", "PipePoissonFunction", "CICDeposit", "solve_batched", "PipeError",
-           "field_energy"]
+__all__ = ["PipeSolver", "PipePoissonFunction", "CICDeposit", "solve_batched", "batch_status",
+           "batch_inject_fault", "PipeError", "field_energy"]
 
 
 def _stream_ptr(stream):
@@ -135,13 +135,13 @@ class PipeSolver:
 
     @property
     def plan(self):
-        z, h, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        check(self.lib.pipe_get_plan(self.handle, ctypes.byref(z), ctypes.byref(h), ctypes.byref(t)),
-              "pipe_get_plan")
-        return {"z_warps": z.value, "t_h": h.value, "t_threads": t.value}
+        z, zp, h, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self.lib.pipe_get_plan(self.handle, ctypes.byref(z), ctypes.byref(zp), ctypes.byref(h),
+                                     ctypes.byref(t)), "pipe_get_plan")
+        return {"z_warps": z.value, "z_pipe": zp.value, "t_h": h.value, "t_threads": t.value}
 
-    def set_plan(self, z_warps, t_h, t_threads):
-        check(self.lib.pipe_set_plan(self.handle, int(z_warps), int(t_h), int(t_threads)),
+    def set_plan(self, z_warps=8, z_pipe=1, t_h=1, t_threads=256):
+        check(self.lib.pipe_set_plan(self.handle, int(z_warps), int(z_pipe), int(t_h), int(t_threads)),
               "pipe_set_plan")
 
     def cic_deposit(self, xyz: torch.Tensor, charge: float, out: torch.Tensor | None = None,
@@ -187,6 +187,14 @@ def batch_status(solvers):
     n = len(solvers)
     hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
     return lib.pipe_batch_status(hs, n)
+
+
+def batch_inject_fault(solvers, drop_stage: int, spin_limit: int):
+    """Test hook: the next batched call with these solvers drops one stage."""
+    lib = _lib.load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    check(lib.pipe_batch_inject_fault(hs, n, int(drop_stage), int(spin_limit)), "pipe_batch_inject_fault")
 
 
 class PipePoissonFunction(torch.autograd.Function):

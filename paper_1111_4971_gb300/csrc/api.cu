@@ -145,10 +145,10 @@ template <typename T>
 int run_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStream_t st) {
   SolveArgs<T> a = make_args<T>(h, rho, phi, h->work);
   cudaError_t e;
-  const int zw = h->plan.z_warps;
-  if ((e = launch_z<T>(true, zw, adjoint, a, st)) != cudaSuccess) return status_of(e);
+  const int zw = h->plan.z_warps, zp = h->plan.z_pipe;
+  if ((e = launch_z<T>(true, zw, zp, adjoint, a, st)) != cudaSuccess) return status_of(e);
   if ((e = transverse_stage<T>(h, adjoint, a, st)) != cudaSuccess) return status_of(e);
-  if ((e = launch_z<T>(false, zw, adjoint, a, st)) != cudaSuccess) return status_of(e);
+  if ((e = launch_z<T>(false, zw, zp, adjoint, a, st)) != cudaSuccess) return status_of(e);
   return PIPE_OK;
 }
 
@@ -343,9 +343,9 @@ int pipe_stage_z_forward(pipe_handle* h, const void* rho, void* spec, int adjoin
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (h->grid.dtype == PIPE_F64)
-    e = launch_z<double>(true, h->plan.z_warps, adjoint != 0, make_args<double>(h, rho, nullptr, spec), s);
+    e = launch_z<double>(true, h->plan.z_warps, h->plan.z_pipe, adjoint != 0, make_args<double>(h, rho, nullptr, spec), s);
   else
-    e = launch_z<float>(true, h->plan.z_warps, adjoint != 0, make_args<float>(h, rho, nullptr, spec), s);
+    e = launch_z<float>(true, h->plan.z_warps, h->plan.z_pipe, adjoint != 0, make_args<float>(h, rho, nullptr, spec), s);
   return status_of(e);
 }
 
@@ -372,9 +372,9 @@ int pipe_stage_z_inverse(pipe_handle* h, const void* spec, void* phi, int adjoin
   cudaError_t e;
   void* sp = const_cast<void*>(spec);
   if (h->grid.dtype == PIPE_F64)
-    e = launch_z<double>(false, h->plan.z_warps, adjoint != 0, make_args<double>(h, nullptr, phi, sp), s);
+    e = launch_z<double>(false, h->plan.z_warps, h->plan.z_pipe, adjoint != 0, make_args<double>(h, nullptr, phi, sp), s);
   else
-    e = launch_z<float>(false, h->plan.z_warps, adjoint != 0, make_args<float>(h, nullptr, phi, sp), s);
+    e = launch_z<float>(false, h->plan.z_warps, h->plan.z_pipe, adjoint != 0, make_args<float>(h, nullptr, phi, sp), s);
   return status_of(e);
 }
 

@@ -1,15 +1,492 @@
-// Batched solves and the autotuner (filled in below the single-solve path).
+// Batched solves: many independent pipe solves (different grids, geometries,
+// Green functions) in one persistent kernel launch.
+//
+// The launch runs one 256-thread CTA per SM (as many as are co-resident).
+// CTAs take items (a group of z-forward tiles, one transverse kz plane, or a
+// group of z-inverse tiles of one solve) from a work list with an atomic
+// counter.  Every item appears in the list after all items it depends on,
+// so an item only ever waits for items that were handed out before it and
+// are being processed by running CTAs: the launch cannot deadlock.  A transverse item of solve s waits until all
+// z-forward tiles of s are done, a z-inverse item until all planes of s are
+// done; completion is counted per solve and stage (release: fence + atomic
+// add; acquire: ld.acquire.gpu).  Every wait is bounded: after spin_limit
+// polls (or once another wait has failed) the CTA records PIPE_ETIMEOUT in
+// the status word, skips the item and continues, so the kernel always ends.
+//
+// Every item runs the same device routine as the per-stage kernels with the
+// shape used by single solves of that size (z: 8 warps per tile; transverse:
+// one 256-thread CTA per plane), so batched and single solves give the same
+// bits.
 #include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <vector>
 
 #include "../../include/pipe_poisson.h"
 #include "handle.cuh"
+#include "tsym_impl.cuh"
+#include "zfft_impl.cuh"
 
 namespace pp {
-void batch_release(pipe_handle*) {}
+
+constexpr int kMaxBatch = 128;
+constexpr int kBatchThreads = 256;
+constexpr int kBatchZWarps = 8;
+
+template <typename T>
+struct BatchParams {
+  const SolveArgs<T>* solves;   // [n], rho/phi taken from the arrays below
+  const int2* items;            // [total]: (solve, stage << 24 | index)
+  const int2* need;             // [n]: (z-forward items, transverse items) of each solve
+  const int2* per;              // [n]: (tiles per z item, planes per transverse item)
+  int* done;                    // [n][2]: completed z-forward tiles, planes
+  int* counter;                 // next item
+  int* status;                  // PIPE_OK or PIPE_ETIMEOUT
+  int total;
+  int n;
+  long long spin_limit;
+  int drop_stage;               // test hook: items of this stage are skipped (-1: none)
+  const T* rho[kMaxBatch];
+  T* phi[kMaxBatch];
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// a z item is `per` consecutive tiles
+template <typename T, int NZ>
+constexpr bool z_pipe_fits() {
+  using Cfg = ZCfg<T, NZ, kBatchZWarps>;
+  return Cfg::fwd_pipe_smem() <= kMaxSmem && Cfg::inv_pipe_smem() <= kMaxSmem;
+}
+
+template <typename T, int NZ>
+__device__ __noinline__ void z_item(bool forward, const SolveArgs<T>& a, int item, int per,
+                                    unsigned char* smem) {
+  const int ntiles = a.nx * a.ny / ZCfg<T, NZ, kBatchZWarps>::COLS;
+  const int first = item * per;
+  const int count = (ntiles - first) < per ? (ntiles - first) : per;
+  if constexpr (z_pipe_fits<T, NZ>()) {          // the pipelined multi-tile routine
+    if (forward) zfwd_tiles_pipe<T, NZ, kBatchZWarps, false>(a, first, 1, count, smem);
+    else zinv_tiles_pipe<T, NZ, kBatchZWarps, false>(a, first, 1, count, smem);
+  } else {
+    for (int k = 0; k < count; ++k) {
+      if (k) __syncthreads();
+      if (forward) zfwd_tile<T, NZ, kBatchZWarps, false>(a, first + k, smem);
+      else zinv_tile<T, NZ, kBatchZWarps, false>(a, first + k, smem);
+    }
+  }
+}
+
+// a transverse item is `per` consecutive kz planes
+template <typename T, int N>
+__device__ __noinline__ void t_item(const SolveArgs<T>& a, int item, int per, unsigned char* smem) {
+  for (int k = 0; k < per; ++k) {
+    const int kz = item * per + k;
+    if (kz > a.nz) break;
+    if (k) __syncthreads();
+    tsym_plane<T, N, 1, kBatchThreads, false>(a, kz, smem);
+  }
+}
+
+template <typename T>
+__device__ void run_item(int stage, const SolveArgs<T>& a, int idx, int per, unsigned char* smem) {
+  if (stage == 1) {
+    switch (a.nx) {
+      case 16: t_item<T, 16>(a, idx, per, smem); break;
+      case 32: t_item<T, 32>(a, idx, per, smem); break;
+      case 64: t_item<T, 64>(a, idx, per, smem); break;
+      case 128: t_item<T, 128>(a, idx, per, smem); break;
+      default: break;
+    }
+    return;
+  }
+  const bool fwd = (stage == 0);
+  switch (a.nz) {
+    case 32: z_item<T, 32>(fwd, a, idx, per, smem); break;
+    case 64: z_item<T, 64>(fwd, a, idx, per, smem); break;
+    case 128: z_item<T, 128>(fwd, a, idx, per, smem); break;
+    case 256: z_item<T, 256>(fwd, a, idx, per, smem); break;
+    case 512: z_item<T, 512>(fwd, a, idx, per, smem); break;
+    case 1024: z_item<T, 1024>(fwd, a, idx, per, smem); break;
+    default: break;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads, 1) batched_kernel(BatchParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  __shared__ int s_ok;
+  __shared__ int s_next;
+  if (threadIdx.x == 0) s_item = atomicAdd(p.counter, 1);
+  __syncthreads();
+  for (;;) {
+    const int it = s_item;
+    if (it >= p.total) return;
+    // claim the next item now; the atomic's latency overlaps this item's work
+    if (threadIdx.x == 0) s_next = atomicAdd(p.counter, 1);
+    const int2 d = p.items[it];
+    const int s = d.x, stage = d.y >> 24, idx = d.y & 0xffffff;
+    if (threadIdx.x == 0) {
+      int ok = (stage != p.drop_stage);
+      if (ok && stage > 0) {
+        const int need = (stage == 1) ? p.need[s].x : p.need[s].y;
+        const int* flag = &p.done[2 * s + stage - 1];
+        long long polls = 0;
+        while (ld_acquire(flag) < need) {
+          if (ld_acquire(p.status) != PIPE_OK || ++polls > p.spin_limit) {
+            atomicCAS(p.status, PIPE_OK, PIPE_ETIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(200);
+        }
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (s_ok) {
+      SolveArgs<T> a = p.solves[s];
+      a.rho = p.rho[s];
+      a.phi = p.phi[s];
+      run_item<T>(stage, a, idx, stage == 1 ? p.per[s].y : p.per[s].x, smem_raw);
+      __syncthreads();
+      if (threadIdx.x == 0 && stage < 2) {
+        __threadfence();
+        atomicAdd(&p.done[2 * s + stage], 1);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = s_next;
+    __syncthreads();
+  }
+}
+
+// shared memory of the persistent CTA: the largest item routine of the batch
+template <typename T>
+size_t item_smem(int nx, int nz) {
+  size_t z = 0, t = 0;
+  auto zs = [](auto cfg, bool pipe) {
+    using C = decltype(cfg);
+    if (!pipe) return C::smem_bytes();
+    return C::fwd_pipe_smem() > C::inv_pipe_smem() ? C::fwd_pipe_smem() : C::inv_pipe_smem();
+  };
+  switch (nz) {
+    case 32: z = zs(ZCfg<T, 32, kBatchZWarps>{}, z_pipe_fits<T, 32>()); break;
+    case 64: z = zs(ZCfg<T, 64, kBatchZWarps>{}, z_pipe_fits<T, 64>()); break;
+    case 128: z = zs(ZCfg<T, 128, kBatchZWarps>{}, z_pipe_fits<T, 128>()); break;
+    case 256: z = zs(ZCfg<T, 256, kBatchZWarps>{}, z_pipe_fits<T, 256>()); break;
+    case 512: z = zs(ZCfg<T, 512, kBatchZWarps>{}, z_pipe_fits<T, 512>()); break;
+    case 1024: z = zs(ZCfg<T, 1024, kBatchZWarps>{}, z_pipe_fits<T, 1024>()); break;
+  }
+  switch (nx) {
+    case 16: t = TSymCfg<T, 16, 1, kBatchThreads>::smem_bytes(); break;
+    case 32: t = TSymCfg<T, 32, 1, kBatchThreads>::smem_bytes(); break;
+    case 64: t = TSymCfg<T, 64, 1, kBatchThreads>::smem_bytes(); break;
+    case 128: t = TSymCfg<T, 128, 1, kBatchThreads>::smem_bytes(); break;
+  }
+  return z > t ? z : t;
+}
+
+template <typename T>
+int z_cols(int nz) {
+  switch (nz) {
+    case 32: return ZCfg<T, 32, kBatchZWarps>::COLS;
+    case 64: return ZCfg<T, 64, kBatchZWarps>::COLS;
+    case 128: return ZCfg<T, 128, kBatchZWarps>::COLS;
+    case 256: return ZCfg<T, 256, kBatchZWarps>::COLS;
+    case 512: return ZCfg<T, 512, kBatchZWarps>::COLS;
+    case 1024: return ZCfg<T, 1024, kBatchZWarps>::COLS;
+  }
+  return 0;
+}
+
+// the work lists of one handle set, built and timed on first use, kept by handles[0]
+struct BatchPlan {
+  int n = 0;
+  int dtype = 0;
+  pipe_handle* handles[kMaxBatch] = {};
+  void* solves = nullptr;    // SolveArgs<T>[n]
+  int2* lists[3] = {nullptr, nullptr, nullptr};   // candidate work lists
+  int2* items = nullptr;     // the chosen one
+  bool tuned = false;
+  int2* need = nullptr;
+  int2* per = nullptr;
+  int* words = nullptr;      // done[2n], counter, status
+  int total = 0;
+  size_t smem = 0;
+  int grid = 0;
+  int order = 0;                // chosen work-list order
+  int drop_stage = -1;          // fault injection for the next launch only
+  long long spin_limit = 1ll << 22;
+};
+
+void batch_release(pipe_handle* h) {
+  if (!h || !h->batch) return;
+  BatchPlan* b = static_cast<BatchPlan*>(h->batch);
+  cudaFree(b->solves);
+  for (int k = 0; k < 3; ++k) cudaFree(b->lists[k]);
+  cudaFree(b->need);
+  cudaFree(b->per);
+  cudaFree(b->words);
+  delete b;
+  h->batch = nullptr;
+}
+
+template <typename T>
+SolveArgs<T> batch_args(pipe_handle* h);
+template <>
+SolveArgs<float> batch_args<float>(pipe_handle* h) {
+  SolveArgs<float> a{};
+  a.work = static_cast<float2*>(h->work); a.green = h->green32;
+  a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32; a.tw_t2 = h->tw_t2_32;
+  a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
+  a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  return a;
+}
+template <>
+SolveArgs<double> batch_args<double>(pipe_handle* h) {
+  SolveArgs<double> a{};
+  a.work = static_cast<double2*>(h->work); a.green = h->green64;
+  a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64; a.tw_t2 = h->tw_t2_64;
+  a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
+  a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  return a;
+}
+
+// Work lists.  z items group tiles so that a solve has at most about 256 of
+// them; transverse items group small planes.  Three orders are built and
+// the first launch times each and keeps the fastest (the autotuner's choice
+// for this handle set):
+//   0 stage-major: every z-forward item, then every transverse item, then
+//     every z-inverse item (solves largest first within a stage);
+//   1 pipelined: wave w holds the z-forward items of solve w, the transverse
+//     items of solve w-2 and the z-inverse items of solve w-4, so that
+//     memory-bound and compute-bound items run at the same time;
+//   2 L2-local: solves whose z spectrum is a sizeable part of L2 run stage
+//     after stage, one at a time, so the spectrum stays in L2 between
+//     stages; the small solves (pipelined among themselves) fill the gaps.
+// In every order an item appears after all items it waits for.
+template <typename T>
+int build_plan(pipe_handle* const* hs, int n, BatchPlan* b) {
+  std::vector<SolveArgs<T>> solves(n);
+  std::vector<int2> need(n);
+  std::vector<int2> per(n);
+  std::vector<int> order(n);
+  size_t smem = 0;
+  for (int s = 0; s < n; ++s) {
+    solves[s] = batch_args<T>(hs[s]);
+    const int nt = hs[s]->grid.nx * hs[s]->grid.ny / z_cols<T>(hs[s]->grid.nz);
+    const int nx = hs[s]->grid.nx, planes = hs[s]->grid.nz + 1;
+    const int pz = nt > 256 ? nt / 256 : 1;
+    const int pt = nx >= 128 ? 1 : (nx >= 64 ? 2 : 8);   // about the work of a 128^2 plane
+    per[s] = make_int2(pz, pt);
+    need[s] = make_int2((nt + pz - 1) / pz, (planes + pt - 1) / pt);
+    const size_t m = item_smem<T>(hs[s]->grid.nx, hs[s]->grid.nz);
+    smem = m > smem ? m : smem;
+    order[s] = s;
+  }
+  auto cost = [&](int s) {
+    return double(hs[s]->grid.nx) * hs[s]->grid.ny * hs[s]->grid.nz;
+  };
+  for (int i = 1; i < n; ++i)            // largest first (stable)
+    for (int j = i; j > 0 && cost(order[j]) > cost(order[j - 1]); --j) std::swap(order[j], order[j - 1]);
+  auto append = [&](std::vector<int2>& dst, int s, int stage) {
+    const int cnt = (stage == 1) ? need[s].y : need[s].x;
+    for (int i = 0; i < cnt; ++i) dst.push_back(make_int2(s, (stage << 24) | i));
+  };
+  auto pipelined = [&](const std::vector<int>& list, std::vector<int2>& dst) {
+    constexpr int LAG = 2;
+    const int m = int(list.size());
+    for (int w = 0; w < m + 2 * LAG; ++w)
+      for (int stage = 0; stage < 3; ++stage) {
+        const int k = w - LAG * stage;
+        if (k >= 0 && k < m) append(dst, list[k], stage);
+      }
+  };
+  std::vector<int2> lists[3];
+  for (int stage = 0; stage < 3; ++stage)
+    for (int k = 0; k < n; ++k) append(lists[0], order[k], stage);
+  pipelined(order, lists[1]);
+  {
+    const double l2_share = 16.0 * 1024 * 1024;
+    std::vector<int> large, small;
+    for (int k = 0; k < n; ++k) {
+      const int s = order[k];
+      const double bytes = double(hs[s]->grid.nx) * hs[s]->grid.ny * (hs[s]->grid.nz + 1) * 2 * sizeof(T);
+      (bytes > l2_share ? large : small).push_back(s);
+    }
+    std::vector<int2> fill;
+    pipelined(small, fill);
+    const int slots = 3 * int(large.size());
+    size_t f = 0;
+    for (int k = 0; k < int(large.size()); ++k)
+      for (int stage = 0; stage < 3; ++stage) {
+        append(lists[2], large[k], stage);
+        const size_t until = fill.size() * size_t(3 * k + stage + 1) / size_t(slots);
+        for (; f < until; ++f) lists[2].push_back(fill[f]);
+      }
+    for (; f < fill.size(); ++f) lists[2].push_back(fill[f]);
+  }
+  std::vector<int2>& items = lists[0];
+  b->total = int(items.size());
+  b->smem = smem;
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->solves, sizeof(SolveArgs<T>) * n)) != cudaSuccess) return PIPE_ENOMEM;
+  for (int k = 0; k < 3; ++k) {
+    if ((e = cudaMalloc(&b->lists[k], sizeof(int2) * items.size())) != cudaSuccess) return PIPE_ENOMEM;
+    if (cudaMemcpy(b->lists[k], lists[k].data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return PIPE_ECUDA;
+  }
+  b->items = b->lists[0];
+  if ((e = cudaMalloc(&b->need, sizeof(int2) * n)) != cudaSuccess) return PIPE_ENOMEM;
+  if ((e = cudaMalloc(&b->per, sizeof(int2) * n)) != cudaSuccess) return PIPE_ENOMEM;
+  if ((e = cudaMalloc(&b->words, sizeof(int) * (2 * n + 2))) != cudaSuccess) return PIPE_ENOMEM;
+  if (cudaMemcpy(b->solves, solves.data(), sizeof(SolveArgs<T>) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->need, need.data(), sizeof(int2) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->per, per.data(), sizeof(int2) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(b->words, 0, sizeof(int) * (2 * n + 2)) != cudaSuccess)
+    return PIPE_ECUDA;
+  if (smem > kMaxSmem) return PIPE_EUNSUPPORTED;
+  if (cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+      cudaSuccess)
+    return PIPE_ECUDA;
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T>, kBatchThreads, smem) !=
+          cudaSuccess || per_sm < 1)
+    return PIPE_ECUDA;
+  b->grid = sms * per_sm;
+  return PIPE_OK;
+}
+
+template <typename T>
+int launch_batch(BatchPlan* b, const void* const* rho, void* const* phi, cudaStream_t st) {
+  BatchParams<T> p;
+  p.solves = static_cast<const SolveArgs<T>*>(b->solves);
+  p.items = b->items;
+  p.need = b->need;
+  p.per = b->per;
+  p.done = b->words;
+  p.counter = b->words + 2 * b->n;
+  p.status = b->words + 2 * b->n + 1;
+  p.total = b->total;
+  p.n = b->n;
+  p.spin_limit = b->spin_limit;      // default 2^22 polls of >= 200 ns: about a second
+  p.drop_stage = b->drop_stage;
+  b->drop_stage = -1;
+  b->spin_limit = 1ll << 22;
+  for (int s = 0; s < b->n; ++s) {
+    p.rho[s] = static_cast<const T*>(rho[s]);
+    p.phi[s] = static_cast<T*>(phi[s]);
+  }
+  for (int s = b->n; s < kMaxBatch; ++s) {
+    p.rho[s] = nullptr;
+    p.phi[s] = nullptr;
+  }
+  if (cudaMemsetAsync(b->words, 0, sizeof(int) * (2 * b->n + 2), st) != cudaSuccess) return PIPE_ECUDA;
+  batched_kernel<T><<<b->grid, kBatchThreads, b->smem, st>>>(p);
+  return cudaGetLastError() == cudaSuccess ? PIPE_OK : PIPE_ECUDA;
+}
+
 }  // namespace pp
 
-extern "C" int pipe_poisson_solve_batched(pipe_handle* const*, const void* const*, void* const*, int,
-                                          void*) {
-  return PIPE_EUNSUPPORTED;
+using namespace pp;
+
+extern "C" int pipe_poisson_solve_batched(pipe_handle* const* handles, const void* const* rho,
+                                          void* const* phi, int n, void* stream) {
+  if (!handles || !rho || !phi || n < 1) return PIPE_EINVAL;
+  if (n > kMaxBatch) return PIPE_EUNSUPPORTED;
+  for (int s = 0; s < n; ++s) {
+    if (!handles[s] || !rho[s] || !phi[s]) return PIPE_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(rho[s]) | reinterpret_cast<uintptr_t>(phi[s])) % 16) return PIPE_EINVAL;
+    if (handles[s]->grid.dtype != handles[0]->grid.dtype || handles[s]->device != handles[0]->device ||
+        !handles[s]->images)
+      return PIPE_EUNSUPPORTED;
+    for (int r = 0; r < s; ++r)
+      if (handles[r] == handles[s]) return PIPE_EINVAL;      // workspaces would collide
+  }
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != handles[0]->device) cudaSetDevice(handles[0]->device);
+  BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
+  bool same = b && b->n == n;
+  for (int s = 0; same && s < n; ++s) same = (b->handles[s] == handles[s]);
+  int st = PIPE_OK;
+  if (!same) {
+    batch_release(handles[0]);
+    b = new (std::nothrow) BatchPlan();
+    if (!b) st = PIPE_ENOMEM;
+    if (st == PIPE_OK) {
+      b->n = n;
+      b->dtype = handles[0]->grid.dtype;
+      for (int s = 0; s < n; ++s) b->handles[s] = handles[s];
+      handles[0]->batch = b;
+      st = b->dtype == PIPE_F64 ? build_plan<double>(handles, n, b) : build_plan<float>(handles, n, b);
+      if (st != PIPE_OK) batch_release(handles[0]);
+    }
+  }
+  if (st == PIPE_OK) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto go = [&]() {
+      return b->dtype == PIPE_F64 ? launch_batch<double>(b, rho, phi, s) : launch_batch<float>(b, rho, phi, s);
+    };
+    if (!b->tuned) {
+      // time each candidate work list once (the results are valid solves)
+      float best = 1e30f;
+      int pick = 0;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      for (int k = 0; k < 3 && st == PIPE_OK; ++k) {
+        b->items = b->lists[k];
+        st = go();                                     // warm-up of this order
+        cudaEventRecord(e0, s);
+        if (st == PIPE_OK) st = go();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st == PIPE_OK && ms < best) { best = ms; pick = k; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      b->items = b->lists[pick];
+      b->order = pick;
+      b->tuned = true;
+    }
+    if (st == PIPE_OK) st = go();
+  }
+  if (cur >= 0 && cur != handles[0]->device) cudaSetDevice(cur);
+  return st;
 }
-extern "C" int pipe_batch_status(pipe_handle* const*, int) { return PIPE_OK; }
+
+extern "C" int pipe_batch_status(pipe_handle* const* handles, int n) {
+  if (!handles || n < 1 || !handles[0]) return PIPE_EINVAL;
+  BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
+  if (!b) return PIPE_EINVAL;
+  int status = PIPE_OK;
+  if (cudaMemcpy(&status, b->words + 2 * b->n + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PIPE_ECUDA;
+  return status;
+}
+
+extern "C" int pipe_batch_inject_fault(pipe_handle* const* handles, int n, int drop_stage,
+                                       long long spin_limit) {
+  if (!handles || n < 1 || !handles[0] || drop_stage < 0 || drop_stage > 2 || spin_limit < 0)
+    return PIPE_EINVAL;
+  BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
+  if (!b || b->n != n) return PIPE_EINVAL;
+  for (int s = 0; s < n; ++s)
+    if (b->handles[s] != handles[s]) return PIPE_EINVAL;
+  b->drop_stage = drop_stage;
+  b->spin_limit = spin_limit;
+  return PIPE_OK;
+}

@@ -291,8 +291,10 @@ __device__ __forceinline__ void fft_c2p(V (&v)[PairShape<L>::E], V* scratch, con
 
 // paired spectral layout -> cyclic time layout (the transpose of fft_c2p's
 // index map): y_n = sum_q X(q) w_L^{qn}, times w_{2L}^{n} when ODDP.
+// twT is the same twiddle table transposed, twT[n2*E + k1] = tw[k1*G + n2],
+// so that lanes reading different rows k1 hit different banks.
 template <int L, bool INV, bool ODDP, typename V>
-__device__ __forceinline__ void fft_p2c(V (&v)[PairShape<L>::E], V* scratch, const V* tw, int t) {
+__device__ __forceinline__ void fft_p2c(V (&v)[PairShape<L>::E], V* scratch, const V* twT, int t) {
   constexpr int G = PairShape<L>::G, E = PairShape<L>::E, U = PairShape<L>::U;
 #pragma unroll
   for (int j = 0; j < U; ++j) {
@@ -302,7 +304,7 @@ __device__ __forceinline__ void fft_p2c(V (&v)[PairShape<L>::E], V* scratch, con
       const int r = pair_row<L, ODDP>(t, j, s);
 #pragma unroll
       for (int n2 = 1; n2 < G; ++n2)          // column n2 = 0 of both tables is 1
-        v[(2 * j + s) * G + n2] = cmulc<INV>(v[(2 * j + s) * G + n2], tw[r * G + n2]);
+        v[(2 * j + s) * G + n2] = cmulc<INV>(v[(2 * j + s) * G + n2], twT[n2 * E + r]);
     }
   }
   __syncwarp();

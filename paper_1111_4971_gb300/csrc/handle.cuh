@@ -10,6 +10,7 @@ namespace pp {
 // pipe_autotune).
 struct Plan {
   int z_warps;     // warps per CTA of the z transforms (8 or 16)
+  int z_pipe;      // 1: pipelined multi-tile z kernels, 0: one tile per CTA
   int t_h;         // transverse stage: row blocks per kz plane (CTAs per cluster)
   int t_threads;   // threads per transverse CTA
 };
@@ -31,8 +32,8 @@ struct pipe_handle {
   double2 *tw_t64 = nullptr, *w2_t64 = nullptr, *tw_z64 = nullptr, *w2_z64 = nullptr, *tw_t2_64 = nullptr;
   void* stage_rho = nullptr;   // device staging for pipe_poisson_solve_host
   void* stage_phi = nullptr;
-  pp::Plan plan{8, 1, 256};
-  pp::Plan free_plan{8, 1, 256};   // transverse shape of the free-space stage
+  pp::Plan plan{8, 0, 1, 256};
+  pp::Plan free_plan{8, 0, 1, 256};   // transverse shape of the free-space stage
   void* batch = nullptr;       // batched work list owned by this handle
 };
 

@@ -39,13 +39,20 @@ struct ZCfg {
   static constexpr int CPW = 32 / UNIT;            // columns per warp
   static constexpr int COLS = WARPS * CPW;         // columns per CTA
   static constexpr int THREADS = 32 * WARPS;
-  static constexpr int SPAD = COLS + 1;            // padded staging row (complex)
   static constexpr int GROUPS = THREADS / G;
-  // the FFT scratch tiles and the (nz+1) x COLS staging tile are live at
-  // different times and share the allocation
+  // staging tile, column major [COLS][LDS]: a lane's column is contiguous, and
+  // the odd stride spreads a row (fixed kz, consecutive columns) over the banks
+  static constexpr int LDS = NZ + 1;
+  // single-tile routines: the FFT scratch tiles and the staging tile are live
+  // at different times and share the allocation
   static constexpr size_t SCR = size_t(GROUPS) * S::SSTRIDE;
-  static constexpr size_t STG = size_t(NZ + 1) * SPAD;
+  static constexpr size_t STG = size_t(COLS) * LDS;
   static constexpr size_t smem_bytes() { return sizeof(C2<T>) * (SCR > STG ? SCR : STG); }
+  // pipelined multi-tile routines: the next tile streams into its own buffer
+  // while the current one is transformed
+  static constexpr size_t INW = size_t(COLS) * (NZ / 2);     // packed real input of a tile
+  static constexpr size_t fwd_pipe_smem() { return sizeof(C2<T>) * (2 * INW + SCR + STG); }
+  static constexpr size_t inv_pipe_smem() { return sizeof(C2<T>) * (2 * STG + SCR); }
 };
 
 template <typename T, int NZ, int WARPS, bool CONJ>
@@ -87,7 +94,7 @@ struct TSymCfg {
   static constexpr int YBUF = N * LD;
   static constexpr int GROUPS = THREADS / G;
   static constexpr size_t smem_bytes() {
-    return sizeof(C2<T>) * (size_t(YBUF) + 2 * size_t(L) + size_t(GROUPS) * S::SSTRIDE);
+    return sizeof(C2<T>) * (size_t(YBUF) + 3 * size_t(L) + size_t(GROUPS) * S::SSTRIDE);
   }
 };
 
@@ -96,7 +103,7 @@ __global__ void transverse_kernel(SolveArgs<T> a);
 
 // host launchers (defined next to the kernels)
 template <typename T>
-cudaError_t launch_z(bool forward, int warps, bool conj, const SolveArgs<T>& a, cudaStream_t st);
+cudaError_t launch_z(bool forward, int warps, int pipe, bool conj, const SolveArgs<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_transverse(bool adjoint, int h, int threads, const SolveArgs<T>& a, cudaStream_t st);
 template <typename T>

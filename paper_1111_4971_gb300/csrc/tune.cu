@@ -23,15 +23,19 @@ namespace pp {
 Plan default_plan(int n, int nz, bool f64) {
   Plan p;
   p.z_warps = (!f64 && nz >= 512) ? 16 : 8;
-  if (n < 128) { p.t_h = 1; p.t_threads = 256; }
-  else if (!f64) { p.t_h = 2; p.t_threads = 256; }
-  else { p.t_h = 4; p.t_threads = 128; }
+  // autotuned on GB300 for 128^2 x 1024: FP32 (8 warps, 1 CTA per plane),
+  // FP64 (8 warps, 2-CTA clusters of 128 threads)
+  p.z_warps = 8;
+  p.z_pipe = f64 ? 0 : 1;
+  if (n < 128 || !f64) { p.t_h = 1; p.t_threads = 256; }
+  else { p.t_h = 2; p.t_threads = 128; }
   return p;
 }
 
 Plan default_free_plan(int n, int nz, bool f64) {
   Plan p;
-  p.z_warps = (!f64 && nz >= 512) ? 16 : 8;
+  p.z_warps = 8;
+  p.z_pipe = f64 ? 0 : 1;
   const size_t c = f64 ? 16 : 8;
   p.t_h = (n >= 128 || c * n * (n + 1) > 150 * 1024) ? 2 : 1;
   p.t_threads = 256;
@@ -55,8 +59,9 @@ void load_file_cache() {
   FILE* f = std::fopen(path, "r");
   if (!f) return;
   int n, nz, dt, zw, th, tt;
-  while (std::fscanf(f, "%d %d %d %d %d %d", &n, &nz, &dt, &zw, &th, &tt) == 6)
-    cache()[Key(n, nz, dt)] = Plan{zw, th, tt};
+  int zp;
+  while (std::fscanf(f, "%d %d %d %d %d %d %d", &n, &nz, &dt, &zw, &zp, &th, &tt) == 7)
+    cache()[Key(n, nz, dt)] = Plan{zw, zp, th, tt};
   std::fclose(f);
 }
 
@@ -65,8 +70,8 @@ void save_file_cache(const Key& k, const Plan& p) {
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), p.z_warps,
-               p.t_h, p.t_threads);
+  std::fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), p.z_warps,
+               p.z_pipe, p.t_h, p.t_threads);
   std::fclose(f);
 }
 
@@ -125,14 +130,15 @@ int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
   Plan best = h->images ? h->plan : h->free_plan;
   float bz = 1e30f, bt = 1e30f;
   const int reps = 5;
-  for (int zw : {8, 16}) {
-    float ms = time_ms([&] {
-      cudaError_t e = launch_z<T>(true, zw, false, a, st);
-      if (e != cudaSuccess) return e;
-      return launch_z<T>(false, zw, false, a, st);
-    }, st, reps);
-    if (ms > 0 && ms < bz) { bz = ms; best.z_warps = zw; }
-  }
+  for (int zw : {8, 16})
+    for (int zp : {0, 1}) {
+      float ms = time_ms([&] {
+        cudaError_t e = launch_z<T>(true, zw, zp, false, a, st);
+        if (e != cudaSuccess) return e;
+        return launch_z<T>(false, zw, zp, false, a, st);
+      }, st, reps);
+      if (ms > 0 && ms < bz) { bz = ms; best.z_warps = zw; best.z_pipe = zp; }
+    }
   if (h->images) {
     const int shapes[6][2] = {{1, 128}, {1, 256}, {2, 128}, {2, 256}, {4, 128}, {4, 256}};
     for (auto& sh : shapes) {
@@ -168,7 +174,7 @@ extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
     auto it = cache().find(k);
     if (it != cache().end()) {
       if (h->images) h->plan = it->second;
-      else { h->plan.z_warps = it->second.z_warps; h->free_plan = it->second; }
+      else { h->plan.z_warps = it->second.z_warps; h->plan.z_pipe = it->second.z_pipe; h->free_plan = it->second; }
       return PIPE_OK;
     }
   }
@@ -181,28 +187,33 @@ extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
   if (dev >= 0 && dev != h->device) cudaSetDevice(dev);
   if (s != PIPE_OK) return s;
   if (h->images) h->plan = p;
-  else { h->plan.z_warps = p.z_warps; h->free_plan = p; }
+  else { h->plan.z_warps = p.z_warps; h->plan.z_pipe = p.z_pipe; h->free_plan = p; }
   std::lock_guard<std::mutex> lk(g_mu);
   cache()[k] = p;
   save_file_cache(k, p);
   return PIPE_OK;
 }
 
-extern "C" int pipe_get_plan(pipe_handle* h, int* z_warps, int* t_h, int* t_threads) {
-  if (!h || !z_warps || !t_h || !t_threads) return PIPE_EINVAL;
+extern "C" int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h, int* t_threads) {
+  if (!h || !z_warps || !z_pipe || !t_h || !t_threads) return PIPE_EINVAL;
   const Plan& p = h->images ? h->plan : h->free_plan;
   *z_warps = h->plan.z_warps;
+  *z_pipe = h->plan.z_pipe;
   *t_h = p.t_h;
   *t_threads = p.t_threads;
   return PIPE_OK;
 }
 
-extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int t_h, int t_threads) {
+extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads) {
   if (!h) return PIPE_EINVAL;
-  if ((z_warps != 8 && z_warps != 16) || (t_h != 1 && t_h != 2 && t_h != 4) ||
+  if ((z_warps != 8 && z_warps != 16) || (z_pipe != 0 && z_pipe != 1) || (t_h != 1 && t_h != 2 && t_h != 4) ||
       (t_threads != 128 && t_threads != 256 && t_threads != 512))
     return PIPE_EINVAL;
-  if (h->images) h->plan = Plan{z_warps, t_h, t_threads};
-  else { h->plan.z_warps = z_warps; h->free_plan = Plan{z_warps, t_h, t_threads}; }
+  if (h->images) h->plan = Plan{z_warps, z_pipe, t_h, t_threads};
+  else {
+    h->plan.z_warps = z_warps;
+    h->plan.z_pipe = z_pipe;
+    h->free_plan = Plan{z_warps, z_pipe, t_h, t_threads};
+  }
   return PIPE_OK;
 }

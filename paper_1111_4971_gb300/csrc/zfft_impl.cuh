@@ -1,0 +1,365 @@
+// Device routines of the z-axis transforms, shared by the per-stage kernels
+// (zfft.cu) and the batched persistent kernel (batched.cu).
+//
+// z-axis transforms of the pipe Poisson solve (Sec. 2 Eq. 10, Appendix A).
+//
+// Forward (zfwd_tile): for every (i,j) column, the 2*nz-point real DFT of the
+// zero-padded column (Eq. A.2; the padded half is never read):
+//     X(kz) = sum_{k<nz} rho_ijk e^{-2 pi i k kz/(2 nz)},   kz = 0..nz
+// Packing z_m = rho_{2m} + i rho_{2m+1} (m < nz/2) turns it into an nz-point
+// complex DFT whose input is half zero; that one splits into two nz/2-point
+// FFTs (even and odd kz of Z, the odd one on the input twisted by w_nz^m).
+// X follows from Z(k) and conj Z(nz-k).  Output is written kz-plane major,
+// work[kz][i*ny + j], through a shared-memory staging tile so that every
+// store is a contiguous run of COLS columns.
+//
+// Inverse (zinv_tile): the transpose of the above for a Hermitian half
+// spectrum: rebuild Z from X(k), X(nz-k), two nz/2-point inverse FFTs, keep
+// only the physical outputs k < nz (the discarded half is never computed).
+// Unnormalised (the 1/(2 nz) lives in the Green spectrum).
+//
+// CONJ gives the transforms of the opposite direction, used by the adjoint:
+// for real data the e^{+} transform is the conjugate of the e^{-} one.
+#pragma once
+
+#include "solver.cuh"
+
+namespace pp {
+
+// asynchronous 16-byte global -> shared copy (L2 only, not cached in L1)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// asynchronous 8-byte global -> shared copy
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+template <typename V>
+__device__ __forceinline__ void cp_async_elem(V* dst, const V* src) {
+  if constexpr (sizeof(V) == 16) cp_async16(dst, src);
+  else cp_async8(dst, src);
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// one CTA of 32*WARPS threads: columns [tile*COLS, (tile+1)*COLS)
+template <typename T, int NZ, int WARPS, bool CONJ>
+__device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsigned char* smem_raw) {
+  using Cfg = ZCfg<T, NZ, WARPS>;
+  using V = C2<T>;
+  constexpr int L = Cfg::L, G = Cfg::G, E = Cfg::E;
+  V* sbase = reinterpret_cast<V*>(smem_raw);
+  V* stage = sbase;                                   // reused after the FFT
+
+  const int ncols = a.nx * a.ny;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int t = lane % G;
+  const int p = (lane / G) & 1;                       // parity of kz produced
+  const int col_local = warp * Cfg::CPW + lane / Cfg::UNIT;
+  const int col0 = tile * Cfg::COLS;
+  const int col = col0 + col_local;
+  const bool valid = col < ncols;
+  V* scratch = sbase + (threadIdx.x / G) * GroupShape<L>::SSTRIDE;
+
+  // packed column, z_m = (rho[2m], rho[2m+1]), m = t + G e
+  V v[E];
+  const V* src = reinterpret_cast<const V*>(a.rho + size_t(valid ? col : 0) * NZ);
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = valid ? __ldg(&src[t + G * e]) : mk<V>(0, 0);
+  if (p) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(&a.w2_z[2 * (t + G * e)]));  // w_nz^m
+  }
+  group_fft<L, false>(v, scratch, a.tw_z, t);        // v[e] = Z(2q + p), q = t + G e
+  const V z0 = v[0];
+  V m[E];
+  mirror_fetch<L>(v, m, t, p, lane - t);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = 2 * (t + G * e) + p;
+    const V zc = cconj(m[e]);
+    const V s = cadd(v[e], zc);
+    const V d = csub(v[e], zc);
+    const V wd = cmul(__ldg(&a.w2_z[k]), d);
+    V x = mk<V>(T(0.5) * (s.x + wd.y), T(0.5) * (s.y - wd.x));   // (s - i w d)/2
+    v[e] = CONJ ? cconj(x) : x;
+  }
+  // X(nz) = Re Z(0) - Im Z(0), held by lane t=0 of the even half
+  const V xN = mk<V>(z0.x - z0.y, T(0));
+
+  // staged, coalesced stores of the whole (nz+1) x COLS tile
+  __syncthreads();                                    // FFT scratch becomes the staging tile
+  V* mycol = stage + col_local * Cfg::LDS;
+#pragma unroll
+  for (int e = 0; e < E; ++e) mycol[2 * (t + G * e) + p] = v[e];
+  if (p == 0 && t == 0) mycol[NZ] = CONJ ? cconj(xN) : xN;
+  __syncthreads();
+  // 16-byte stores: EPV complex (consecutive columns) per vector
+  constexpr int EPV = 16 / int(sizeof(V));
+  constexpr int VPR = Cfg::COLS / EPV;
+  for (int idx = threadIdx.x; idx < (NZ + 1) * VPR; idx += Cfg::THREADS) {
+    const int r = idx / VPR;
+    const int cc = (idx % VPR) * EPV;
+    if (col0 + cc < ncols) {
+      if constexpr (EPV == 2) {
+        const V x0 = stage[cc * Cfg::LDS + r], x1 = stage[(cc + 1) * Cfg::LDS + r];
+        *reinterpret_cast<float4*>(&a.work[size_t(r) * ncols + col0 + cc]) = make_float4(x0.x, x0.y, x1.x, x1.y);
+      } else {
+        a.work[size_t(r) * ncols + col0 + cc] = stage[cc * Cfg::LDS + r];
+      }
+    }
+  }
+}
+
+template <typename T, int NZ, int WARPS, bool CONJ>
+__device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsigned char* smem_raw) {
+  using Cfg = ZCfg<T, NZ, WARPS>;
+  using V = C2<T>;
+  constexpr int L = Cfg::L, G = Cfg::G, E = Cfg::E;
+  V* sbase = reinterpret_cast<V*>(smem_raw);
+  V* stage = sbase;                                   // FFT scratch reuses it afterwards
+
+  const int ncols = a.nx * a.ny;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int t = lane % G;
+  const int p = (lane / G) & 1;
+  const int col_local = warp * Cfg::CPW + lane / Cfg::UNIT;
+  const int col0 = tile * Cfg::COLS;
+  const int col = col0 + col_local;
+  const bool valid = col < ncols;
+  V* scratch = sbase + (threadIdx.x / G) * GroupShape<L>::SSTRIDE;
+
+  // the whole (nz+1) x COLS tile in flight at once (cp.async, one element each)
+  for (int idx = threadIdx.x; idx < (NZ + 1) * Cfg::COLS; idx += Cfg::THREADS) {
+    const int r = idx / Cfg::COLS;
+    const int cc = idx % Cfg::COLS;
+    if (col0 + cc < ncols) cp_async_elem(&stage[cc * Cfg::LDS + r], &a.work[size_t(r) * ncols + col0 + cc]);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const V* mycol = stage + col_local * Cfg::LDS;
+  V v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = mycol[2 * (t + G * e) + p];
+  V xN = mycol[NZ];
+  __syncthreads();                                    // staging tile becomes FFT scratch
+  if (CONJ) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = cconj(v[e]);
+    xN = cconj(xN);
+  }
+  // partner X(nz - k) of every k = 2q + p (q = 0 pairs with X(nz))
+  V m[E];
+  mirror_fetch<L>(v, m, t, p, lane - t);
+  if (p == 0 && t == 0) m[0] = xN;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = 2 * (t + G * e) + p;
+    const V xm = cconj(m[e]);
+    const V s = cadd(v[e], xm);
+    const V d = csub(v[e], xm);
+    const V wd = cmulc<true>(d, __ldg(&a.w2_z[k]));           // w_{2nz}^{-k} d
+    v[e] = mk<V>(s.x - wd.y, s.y + wd.x);                      // s + i w d
+  }
+  group_fft<L, true>(v, scratch, a.tw_z, t);                  // z_p(m), m = t + G e
+  if (p) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], __ldg(&a.w2_z[2 * (t + G * e)]));
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    v[e].x += __shfl_xor_sync(0xffffffffu, v[e].x, G);
+    v[e].y += __shfl_xor_sync(0xffffffffu, v[e].y, G);
+  }
+  if (valid) {
+    V* dst = reinterpret_cast<V*>(a.phi + size_t(col) * NZ);
+#pragma unroll
+    for (int e2 = 0; e2 < E / 2; ++e2) {
+      const int e = e2 + p * (E / 2);
+      const V val = p ? v[e2 + E / 2] : v[e2];
+      dst[t + G * e] = val;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined multi-tile versions: `count` tiles first, first+stride, ...; the
+// input of the next tile is copied (cp.async) into the second buffer while
+// the current tile is transformed, so that one CTA keeps HBM busy on its own.
+// ---------------------------------------------------------------------------
+template <typename T, int NZ, int WARPS, bool CONJ>
+__device__ __forceinline__ void zfwd_tiles_pipe(const SolveArgs<T>& a, int first, int stride, int count,
+                                                unsigned char* smem_raw) {
+  using Cfg = ZCfg<T, NZ, WARPS>;
+  using V = C2<T>;
+  constexpr int L = Cfg::L, G = Cfg::G, E = Cfg::E;
+  constexpr int INW = int(Cfg::INW);
+  V* inb = reinterpret_cast<V*>(smem_raw);                    // [2][COLS][NZ/2]
+  V* scr0 = inb + 2 * INW;
+  V* stage = scr0 + Cfg::SCR;                                  // [COLS][LDS]
+  const int ncols = a.nx * a.ny;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int t = lane % G;
+  const int p = (lane / G) & 1;
+  const int col_local = warp * Cfg::CPW + lane / Cfg::UNIT;
+  V* scratch = scr0 + (threadIdx.x / G) * GroupShape<L>::SSTRIDE;
+  // 16-byte pieces of one tile's input: COLS columns of NZ reals
+  constexpr int PPC = NZ * int(sizeof(T)) / 16;
+  auto issue = [&](int tile, V* buf) {
+    const int col0 = tile * Cfg::COLS;
+    for (int idx = threadIdx.x; idx < Cfg::COLS * PPC; idx += Cfg::THREADS) {
+      const int cc = idx / PPC, piece = idx % PPC;
+      if (col0 + cc < ncols)
+        cp_async16(reinterpret_cast<unsigned char*>(buf + cc * (NZ / 2)) + 16 * piece,
+                   reinterpret_cast<const unsigned char*>(a.rho + size_t(col0 + cc) * NZ) + 16 * piece);
+    }
+    cp_async_commit();
+  };
+  if (count > 0) issue(first, inb);
+  for (int k = 0; k < count; ++k) {
+    const int tile = first + k * stride;
+    const int col0 = tile * Cfg::COLS;
+    if (k + 1 < count) {
+      issue(first + (k + 1) * stride, inb + ((k + 1) & 1) * INW);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const V* src = inb + (k & 1) * INW + col_local * (NZ / 2);
+    V v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = src[t + G * e];
+    if (p) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(&a.w2_z[2 * (t + G * e)]));
+    }
+    group_fft<L, false>(v, scratch, a.tw_z, t);
+    const V z0 = v[0];
+    V m[E];
+    mirror_fetch<L>(v, m, t, p, lane - t);
+    V* mycol = stage + col_local * Cfg::LDS;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int kz = 2 * (t + G * e) + p;
+      const V zc = cconj(m[e]);
+      const V s = cadd(v[e], zc);
+      const V d = csub(v[e], zc);
+      const V wd = cmul(__ldg(&a.w2_z[kz]), d);
+      V x = mk<V>(T(0.5) * (s.x + wd.y), T(0.5) * (s.y - wd.x));
+      mycol[kz] = CONJ ? cconj(x) : x;
+    }
+    if (p == 0 && t == 0) {
+      const V xN = mk<V>(z0.x - z0.y, T(0));
+      mycol[NZ] = CONJ ? cconj(xN) : xN;
+    }
+    __syncthreads();
+    constexpr int EPV = 16 / int(sizeof(V));
+    constexpr int VPR = Cfg::COLS / EPV;
+    for (int idx = threadIdx.x; idx < (NZ + 1) * VPR; idx += Cfg::THREADS) {
+      const int r = idx / VPR;
+      const int cc = (idx % VPR) * EPV;
+      if (col0 + cc < ncols) {
+        if constexpr (EPV == 2) {
+          const V x0 = stage[cc * Cfg::LDS + r], x1 = stage[(cc + 1) * Cfg::LDS + r];
+          *reinterpret_cast<float4*>(&a.work[size_t(r) * ncols + col0 + cc]) =
+              make_float4(x0.x, x0.y, x1.x, x1.y);
+        } else {
+          a.work[size_t(r) * ncols + col0 + cc] = stage[cc * Cfg::LDS + r];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int NZ, int WARPS, bool CONJ>
+__device__ __forceinline__ void zinv_tiles_pipe(const SolveArgs<T>& a, int first, int stride, int count,
+                                                unsigned char* smem_raw) {
+  using Cfg = ZCfg<T, NZ, WARPS>;
+  using V = C2<T>;
+  constexpr int L = Cfg::L, G = Cfg::G, E = Cfg::E;
+  constexpr int STG = int(Cfg::STG);
+  V* stg = reinterpret_cast<V*>(smem_raw);                    // [2][COLS][LDS]
+  V* scr0 = stg + 2 * STG;
+  const int ncols = a.nx * a.ny;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int t = lane % G;
+  const int p = (lane / G) & 1;
+  const int col_local = warp * Cfg::CPW + lane / Cfg::UNIT;
+  V* scratch = scr0 + (threadIdx.x / G) * GroupShape<L>::SSTRIDE;
+  auto issue = [&](int tile, V* buf) {
+    const int col0 = tile * Cfg::COLS;
+    for (int idx = threadIdx.x; idx < (NZ + 1) * Cfg::COLS; idx += Cfg::THREADS) {
+      const int r = idx / Cfg::COLS, cc = idx % Cfg::COLS;
+      if (col0 + cc < ncols) cp_async_elem(&buf[cc * Cfg::LDS + r], &a.work[size_t(r) * ncols + col0 + cc]);
+    }
+    cp_async_commit();
+  };
+  if (count > 0) issue(first, stg);
+  for (int k = 0; k < count; ++k) {
+    const int tile = first + k * stride;
+    const int col = tile * Cfg::COLS + col_local;
+    if (k + 1 < count) {
+      issue(first + (k + 1) * stride, stg + ((k + 1) & 1) * STG);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const V* mycol = stg + (k & 1) * STG + col_local * Cfg::LDS;
+    V v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = mycol[2 * (t + G * e) + p];
+    V xN = mycol[NZ];
+    if (CONJ) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = cconj(v[e]);
+      xN = cconj(xN);
+    }
+    V m[E];
+    mirror_fetch<L>(v, m, t, p, lane - t);
+    if (p == 0 && t == 0) m[0] = xN;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int kz = 2 * (t + G * e) + p;
+      const V xm = cconj(m[e]);
+      const V s = cadd(v[e], xm);
+      const V d = csub(v[e], xm);
+      const V wd = cmulc<true>(d, __ldg(&a.w2_z[kz]));
+      v[e] = mk<V>(s.x - wd.y, s.y + wd.x);
+    }
+    group_fft<L, true>(v, scratch, a.tw_z, t);
+    if (p) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], __ldg(&a.w2_z[2 * (t + G * e)]));
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      v[e].x += __shfl_xor_sync(0xffffffffu, v[e].x, G);
+      v[e].y += __shfl_xor_sync(0xffffffffu, v[e].y, G);
+    }
+    if (col < ncols) {
+      V* dst = reinterpret_cast<V*>(a.phi + size_t(col) * NZ);
+#pragma unroll
+      for (int e2 = 0; e2 < E / 2; ++e2) {
+        const int e = e2 + p * (E / 2);
+        dst[t + G * e] = p ? v[e2 + E / 2] : v[e2];
+      }
+    }
+    __syncthreads();                 // this buffer is refilled by the next issue
+  }
+}
+
+}  // namespace pp

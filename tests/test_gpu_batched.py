@@ -1,0 +1,122 @@
+"""Batched persistent launch: same bits as single solves, graph replay, and the
+bounded-wait failure path (a dropped stage makes the waits give up)."""
+import numpy as np
+import pytest
+import torch
+
+from inputs import bunches
+from inputs.bunches import cell_centred, random_density
+from oracle import pipe
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1111_4971_gb300 import build
+    build.build()
+
+
+def make_set(count, seed=4, dtype=torch.float32):
+    from paper_1111_4971_gb300 import PipeSolver
+    items = bunches.workload_batched_96(seed=seed, count=count)
+    solvers, rhos = [], []
+    for it in items:
+        s = PipeSolver(it["geom"], it["grid"], igf=True, dtype=dtype)
+        s.set_plan(z_warps=8, z_pipe=1, t_h=1, t_threads=256)   # the shape the batched kernel runs
+        solvers.append(s)
+        rhos.append(torch.tensor(it["rho"], dtype=dtype, device="cuda"))
+    return items, solvers, rhos
+
+
+def test_batched_equals_loop_bitwise_and_oracle():
+    from paper_1111_4971_gb300 import batch_status, solve_batched
+    items, solvers, rhos = make_set(10)
+    phis_b = [s.empty() for s in solvers]
+    solve_batched(solvers, rhos, phis_b)
+    torch.cuda.synchronize()
+    assert batch_status(solvers) == 0
+    for s, r, pb in zip(solvers, rhos, phis_b):
+        pl = s.solve(r)
+        torch.cuda.synchronize()
+        assert torch.equal(pl, pb)
+    # the smallest solves against the oracle
+    for it, pb in zip(items, phis_b):
+        if it["grid"].nx <= 32:
+            want = pipe.fft_solve(it["rho"], it["geom"], it["grid"], 1)
+            got = pb.double().cpu().numpy()
+            assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
+
+
+def test_batched_fp64_small_sizes():
+    from paper_1111_4971_gb300 import PipeSolver, batch_status, solve_batched
+    cases = [cell_centred(1.0, 1.0, 16, 16, 32, 0.05), cell_centred(2.0, 1.0, 32, 32, 64, 0.07),
+             cell_centred(1.5, 1.0, 64, 64, 32, 0.03)]
+    solvers, rhos, wants = [], [], []
+    for k, (g, gr) in enumerate(cases):
+        s = PipeSolver(g, gr, igf=True, dtype=torch.float64)
+        s.set_plan(z_warps=8, z_pipe=1, t_h=1, t_threads=256)
+        rho = random_density(gr.shape, 30 + k)
+        solvers.append(s)
+        rhos.append(torch.tensor(rho, dtype=torch.float64, device="cuda"))
+        wants.append(pipe.fft_solve(rho, g, gr, 1))
+    phis = [s.empty() for s in solvers]
+    solve_batched(solvers, rhos, phis)
+    torch.cuda.synchronize()
+    assert batch_status(solvers) == 0
+    for p, w in zip(phis, wants):
+        assert np.linalg.norm(p.cpu().numpy() - w) <= 1e-12 * np.linalg.norm(w)
+
+
+def test_batched_graph_replay():
+    from paper_1111_4971_gb300 import batch_status, solve_batched
+    items, solvers, rhos = make_set(6, seed=7)
+    phis = [s.empty() for s in solvers]
+    solve_batched(solvers, rhos, phis)          # builds the work list
+    torch.cuda.synchronize()
+    ref = [p.clone() for p in phis]
+    for p in phis:
+        p.zero_()
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            solve_batched(solvers, rhos, phis, stream=stream)
+    for _ in range(2):
+        for p in phis:
+            p.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert batch_status(solvers) == 0
+        for a, b in zip(phis, ref):
+            assert torch.equal(a, b)
+
+
+def test_batched_wait_timeout_is_reported_and_recovers():
+    from paper_1111_4971_gb300 import batch_inject_fault, batch_status, solve_batched
+    items, solvers, rhos = make_set(4, seed=9)
+    phis = [s.empty() for s in solvers]
+    solve_batched(solvers, rhos, phis)
+    torch.cuda.synchronize()
+    ref = [p.clone() for p in phis]
+    # the z-forward stage is dropped: no transverse wait can be satisfied
+    batch_inject_fault(solvers, 0, 2000)
+    solve_batched(solvers, rhos, phis)
+    torch.cuda.synchronize()
+    assert batch_status(solvers) == 5            # PIPE_ETIMEOUT
+    # the next launch is a normal one again
+    solve_batched(solvers, rhos, phis)
+    torch.cuda.synchronize()
+    assert batch_status(solvers) == 0
+    for a, b in zip(phis, ref):
+        assert torch.equal(a, b)
+
+
+def test_batched_argument_errors():
+    from paper_1111_4971_gb300 import PipeError, solve_batched
+    items, solvers, rhos = make_set(2, seed=11)
+    phis = [s.empty() for s in solvers]
+    with pytest.raises(PipeError):
+        solve_batched([solvers[0], solvers[0]], [rhos[0], rhos[0]], [phis[0], phis[1]])
