@@ -109,6 +109,25 @@ int pipe_poisson_solve(pipe_handle* h, const void* rho, void* phi, void* stream)
  * (dW/drho, backward passes) call.  Same arguments and errors as the solve. */
 int pipe_poisson_adjoint(pipe_handle* h, const void* dphi, void* drho, void* stream);
 
+/* pipe_poisson_solve without any device allocation by the library: the
+ * solve's working buffer (the z half-spectrum, (nz+1)*nx*ny complex values of
+ * the handle's dtype) is a fixed 64 MiB device array that belongs to the
+ * library and stays reserved on every GPU that loads it until the process
+ * exits.  Meant for programs that must not let a library allocate device
+ * memory while they run (a host that keeps the GPU's memory in its own pool,
+ * a loop that cannot risk an allocation stalling or failing): they create the
+ * handle during initialisation and call this afterwards.  The paper has no
+ * counterpart; it is an interface convenience.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current).  All calls share the array: calls whose
+ * kernels overlap on the GPU (other streams or handles at the same time) race
+ * and corrupt each other's results.  Nothing needs clearing between calls.
+ * Same arguments as pipe_poisson_solve.  Errors: PIPE_EINVAL (null or
+ * misaligned pointers), PIPE_EUNSUPPORTED when (nz+1)*nx*ny complex values of
+ * the dtype exceed 64 MiB (e.g. 128x128x256 FP32 fits, 128x128x512 FP32 does
+ * not), PIPE_ECUDA. */
+int pipe_poisson_solve_noalloc(pipe_handle* h, const void* rho, void* phi, void* stream);
+
 /* Same as pipe_poisson_solve but rho_host / phi_host are HOST arrays: the
  * library copies rho to the device, solves and copies phi back on `stream`,
  * then synchronises the stream.  Device staging buffers are allocated on the

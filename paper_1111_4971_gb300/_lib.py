@@ -42,6 +42,7 @@ SIGNATURES = {
     "pipe_poisson_solve": (c_int, [H, c_void_p, c_void_p, c_void_p]),
     "pipe_poisson_adjoint": (c_int, [H, c_void_p, c_void_p, c_void_p]),
     "pipe_poisson_solve_host": (c_int, [H, c_void_p, c_void_p, c_void_p]),
+    "pipe_poisson_solve_noalloc": (c_int, [H, c_void_p, c_void_p, c_void_p]),
     "pipe_poisson_solve_batched": (c_int, [POINTER(H), POINTER(c_void_p), POINTER(c_void_p), c_int,
                                            c_void_p]),
     "pipe_batch_status": (c_int, [POINTER(H), c_int]),
