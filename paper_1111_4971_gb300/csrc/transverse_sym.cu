@@ -4,20 +4,22 @@
 
 namespace pp {
 
-template <typename T, int N, int HB, int THREADS, bool ADJ>
-__global__ void __launch_bounds__(THREADS) transverse_sym_kernel(SolveArgs<T> a) {
+// MINB = 2 caps registers so that two CTAs share an SM (where their shared
+// memory also fits)
+template <typename T, int N, int HB, int THREADS, bool ADJ, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) transverse_sym_kernel(SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   tsym_plane<T, N, HB, THREADS, ADJ>(a, blockIdx.x / HB, smem_raw);
 }
 
-template <typename T, int N, int HB, int THREADS, bool ADJ>
+template <typename T, int N, int HB, int THREADS, bool ADJ, int MINB = 1>
 static cudaError_t tslaunch(const SolveArgs<T>& a, cudaStream_t st) {
   using Cfg = TSymCfg<T, N, HB, THREADS>;
   if constexpr (Cfg::smem_bytes() > kMaxSmem || N / HB < 2 || (N < 128 && HB != 1)) {
     return cudaErrorInvalidConfiguration;
   } else {
     const size_t smem = Cfg::smem_bytes();
-    void (*kern)(SolveArgs<T>) = transverse_sym_kernel<T, N, HB, THREADS, ADJ>;
+    void (*kern)(SolveArgs<T>) = transverse_sym_kernel<T, N, HB, THREADS, ADJ, MINB>;
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
@@ -48,8 +50,9 @@ static cudaError_t tslaunch2(bool adjoint, int hb, int threads, const SolveArgs<
   PP_TS_CASE(2, 128)
   PP_TS_CASE(2, 256)
   PP_TS_CASE(4, 128)
-  PP_TS_CASE(4, 256)
 #undef PP_TS_CASE
+  if (hb == 4 && threads == 256)          // 112 KB of shared memory: two CTAs per SM
+    return adjoint ? tslaunch<T, N, 4, 256, true, 2>(a, st) : tslaunch<T, N, 4, 256, false, 2>(a, st);
   return cudaErrorInvalidConfiguration;
 }
 

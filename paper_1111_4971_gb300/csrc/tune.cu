@@ -26,7 +26,7 @@ Plan default_plan(int n, int nz, bool f64) {
   // autotuned on GB300 for 128^2 x 1024: FP32 (8 warps, 1 CTA per plane),
   // FP64 (8 warps, 2-CTA clusters of 128 threads)
   p.z_warps = 8;
-  p.z_pipe = f64 ? 0 : 1;
+  p.z_pipe = 0;
   if (n < 128 || !f64) { p.t_h = 1; p.t_threads = 256; }
   else { p.t_h = 2; p.t_threads = 128; }
   return p;
@@ -35,7 +35,7 @@ Plan default_plan(int n, int nz, bool f64) {
 Plan default_free_plan(int n, int nz, bool f64) {
   Plan p;
   p.z_warps = 8;
-  p.z_pipe = f64 ? 0 : 1;
+  p.z_pipe = 0;
   const size_t c = f64 ? 16 : 8;
   p.t_h = (n >= 128 || c * n * (n + 1) > 150 * 1024) ? 2 : 1;
   p.t_threads = 256;
