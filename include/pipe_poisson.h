@@ -141,8 +141,17 @@ int pipe_poisson_solve_host(pipe_handle* h, const void* rho_host, void* phi_host
  * same solve.  All handles must share one dtype and device, and must not be
  * used concurrently elsewhere.  A wait that gives up records PIPE_ETIMEOUT in
  * the batch status (read with pipe_batch_status after the stream completes).
- * Capturable in a CUDA graph after the first call with the same handle set
- * (the first call builds and uploads the work list; later calls reuse it).
+ * The first call with a handle set builds the work lists and times the ways
+ * of splitting the set between the persistent launch and single-solve launches
+ * issued after it on the same stream (cut-offs: none, then each distinct z
+ * spectrum size from the largest down, at most five; the solves at or above
+ * the cut-off go to single-solve launches) and three work-list orders, keeping
+ * the fastest; those timing runs are valid solves, and the first call
+ * synchronises the stream.  Later calls with the same set reuse the
+ * choice and are capturable in a CUDA graph.  Results equal those of
+ * pipe_poisson_solve up to rounding, and bitwise for FP32 handles whose plan is
+ * z_warps = 16, z_pipe = 0, t_h = 1, t_threads = 512 (the persistent kernel's
+ * shapes).
  * Errors: PIPE_EINVAL (n < 1, null arrays), PIPE_EUNSUPPORTED (mixed dtypes
  * or devices), PIPE_ENOMEM, PIPE_ECUDA. */
 int pipe_poisson_solve_batched(pipe_handle* const* handles, const void* const* rho,
@@ -152,12 +161,27 @@ int pipe_poisson_solve_batched(pipe_handle* const* handles, const void* const* r
  * batch plan: PIPE_OK or PIPE_ETIMEOUT.  Synchronous (copies one word). */
 int pipe_batch_status(pipe_handle* const* handles, int n);
 
+/* The choice the first batched call made for this exact handle set: how many
+ * solves run in the persistent launch (the rest as single-solve launches) and
+ * the work-list order (0 stage-major, 1 pipelined, 2 L2-local).  Errors:
+ * PIPE_EINVAL (null pointers, or no tuned plan for this set). */
+int pipe_batch_plan_info(pipe_handle* const* handles, int n, int* persistent, int* order);
+
+/* Override that choice for later calls with this exact handle set: `variant`
+ * k runs persistent the solves whose z spectrum is smaller than the k-th
+ * largest distinct spectrum size of the set (k = 0: every solve), `order` as
+ * above.  For tests and experiments.  Errors: PIPE_EINVAL (no tuned plan for
+ * this set, k beyond the cut-offs built, order outside 0..2, or order != 0
+ * for a variant with no persistent solve). */
+int pipe_batch_select(pipe_handle* const* handles, int n, int variant, int order);
+
 /* Failure-detection test hook for the batched launch: the NEXT
  * pipe_poisson_solve_batched call with this exact handle set (whose work list
  * must already exist, i.e. after one normal call) skips every item of stage
  * `drop_stage` (0 z-forward, 1 transverse, 2 z-inverse) without counting it
  * and polls at most `spin_limit` times per wait, so the dependent waits give
  * up and the batch status becomes PIPE_ETIMEOUT while the kernel still ends.
+ * That call runs every solve of the set in the persistent launch.
  * The results of that call are undefined.  Errors: PIPE_EINVAL. */
 int pipe_batch_inject_fault(pipe_handle* const* handles, int n, int drop_stage, long long spin_limit);
 

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import PipeError, PipeGeometry, PipeGrid, check
 
 __all__ = ["PipeSolver", "PipePoissonFunction", "CICDeposit", "solve_batched", "batch_status",
-           "batch_inject_fault", "PipeError", "field_energy"]
+           "batch_inject_fault", "batch_plan_info", "batch_select", "PipeError", "field_energy"]
 
 
 def _stream_ptr(stream):
@@ -172,7 +172,8 @@ class PipeSolver:
 
 
 def solve_batched(solvers, rhos, phis, stream=None):
-    """n independent solves in one persistent launch (see pipe_poisson_solve_batched)."""
+    """n independent solves: a persistent launch over a work list, with the
+    largest solves possibly left to single-solve launches (pipe_poisson_solve_batched)."""
     lib = _lib.load()
     n = len(solvers)
     hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
@@ -187,6 +188,24 @@ def batch_status(solvers):
     n = len(solvers)
     hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
     return lib.pipe_batch_status(hs, n)
+
+
+def batch_plan_info(solvers):
+    """(solves in the persistent launch, work-list order) chosen for this set."""
+    lib = _lib.load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    k, o = ctypes.c_int(0), ctypes.c_int(0)
+    check(lib.pipe_batch_plan_info(hs, n, ctypes.byref(k), ctypes.byref(o)), "pipe_batch_plan_info")
+    return k.value, o.value
+
+
+def batch_select(solvers, variant: int, order: int):
+    """Override the tuned split (variant 0: every solve persistent) and work-list order."""
+    lib = _lib.load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    check(lib.pipe_batch_select(hs, n, int(variant), int(order)), "pipe_batch_select")
 
 
 def batch_inject_fault(solvers, drop_stage: int, spin_limit: int):

@@ -79,13 +79,15 @@ int alloc_common(pipe_handle* h) {
   if ((e = cudaMalloc(&h->work, work)) != cudaSuccess) return status_of(e);
   const int n = g.nx, Lz = g.nz / 2;
   // float2 and double2 tables: tw_t (n), w2_t (2n), tw_z (nz/2), w2_z (2nz)
-  const size_t cnt = size_t(n) + 2 * n + Lz + 2 * g.nz + 2 * n;
+  const size_t cnt = size_t(n) + 2 * n + Lz + 2 * g.nz + 2 * n + 2 * n;
   if ((e = cudaMalloc(&h->tab32, cnt * sizeof(float2))) != cudaSuccess) return status_of(e);
   if ((e = cudaMalloc(&h->tab64, cnt * sizeof(double2))) != cudaSuccess) return status_of(e);
   h->tw_t32 = h->tab32; h->w2_t32 = h->tw_t32 + n; h->tw_z32 = h->w2_t32 + 2 * n; h->w2_z32 = h->tw_z32 + Lz;
   h->tw_t2_32 = h->w2_z32 + 2 * g.nz;
+  h->tw_t2c_32 = h->tw_t2_32 + 2 * n;
   h->tw_t64 = h->tab64; h->w2_t64 = h->tw_t64 + n; h->tw_z64 = h->w2_t64 + 2 * n; h->w2_z64 = h->tw_z64 + Lz;
   h->tw_t2_64 = h->w2_z64 + 2 * g.nz;
+  h->tw_t2c_64 = h->tw_t2_64 + 2 * n;
   cudaStream_t st = nullptr;
   launch_tables<float2>(h->tw_t32, h->w2_t32, n, sub_fft_group(n), 2 * n, st);
   launch_tables<float2>(h->tw_z32, h->w2_z32, Lz, sub_fft_group(Lz), 2 * g.nz, st);
@@ -93,6 +95,8 @@ int alloc_common(pipe_handle* h) {
   launch_tables<double2>(h->tw_z64, h->w2_z64, Lz, sub_fft_group(Lz), 2 * g.nz, st);
   launch_tables<float2>(h->tw_t2_32, nullptr, 2 * n, pair_fft_group(2 * n), 0, st);
   launch_tables<double2>(h->tw_t2_64, nullptr, 2 * n, pair_fft_group(2 * n), 0, st);
+  launch_tables<float2>(h->tw_t2c_32, nullptr, 2 * n, sub_fft_group(2 * n), 0, st);
+  launch_tables<double2>(h->tw_t2c_64, nullptr, 2 * n, sub_fft_group(2 * n), 0, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return status_of(e);
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return status_of(e);
   return PIPE_OK;
@@ -119,6 +123,7 @@ SolveArgs<float> make_args<float>(pipe_handle* h, const void* rho, void* phi, vo
   a.work = static_cast<float2*>(work); a.green = h->green32;
   a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32;
   a.tw_t2 = h->tw_t2_32;
+  a.tw_t2c = h->tw_t2c_32;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
@@ -130,6 +135,7 @@ SolveArgs<double> make_args<double>(pipe_handle* h, const void* rho, void* phi, 
   a.work = static_cast<double2*>(work); a.green = h->green64;
   a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64;
   a.tw_t2 = h->tw_t2_64;
+  a.tw_t2c = h->tw_t2c_64;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;

@@ -1,7 +1,7 @@
 // Batched solves: many independent pipe solves (different grids, geometries,
 // Green functions) in one persistent kernel launch.
 //
-// The launch runs one 256-thread CTA per SM (as many as are co-resident).
+// The launch runs one CTA per SM (as many as are co-resident).
 // CTAs take items (a group of z-forward tiles, one transverse kz plane, or a
 // group of z-inverse tiles of one solve) from a work list with an atomic
 // counter.  Every item appears in the list after all items it depends on,
@@ -13,14 +13,16 @@
 // polls (or once another wait has failed) the CTA records PIPE_ETIMEOUT in
 // the status word, skips the item and continues, so the kernel always ends.
 //
-// Every item runs the same device routine as the per-stage kernels with the
-// shape used by single solves of that size (z: 8 warps per tile; transverse:
-// one 256-thread CTA per plane), so batched and single solves give the same
-// bits.
+// The CTA has 512 threads (16 warps; every item routine fits 128 registers).
+// Items run the same device routines as the per-stage kernels: z tiles of 16
+// warps (pipelined where the double buffer fits), transverse planes with the
+// cyclic-layout routine of the (1 CTA, 512 threads) plan; single solves with
+// that transverse plan give the same bits.
 #include <cuda_runtime.h>
 
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/pipe_poisson.h"
@@ -31,8 +33,8 @@
 namespace pp {
 
 constexpr int kMaxBatch = 128;
-constexpr int kBatchThreads = 256;
-constexpr int kBatchZWarps = 8;
+constexpr int kBatchThreads = 512;   // 16 warps: every item routine fits 128 registers
+constexpr int kBatchZWarps = 16;
 
 template <typename T>
 struct BatchParams {
@@ -89,7 +91,7 @@ __device__ __noinline__ void t_item(const SolveArgs<T>& a, int item, int per, un
     const int kz = item * per + k;
     if (kz > a.nz) break;
     if (k) __syncthreads();
-    tsym_plane<T, N, 1, kBatchThreads, false>(a, kz, smem);
+    tsym_cyc_plane<T, N, kBatchThreads, false>(a, kz, smem);
   }
 }
 
@@ -123,14 +125,23 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batched_kernel(BatchParams<T
   __shared__ int s_item;
   __shared__ int s_ok;
   __shared__ int s_next;
-  if (threadIdx.x == 0) s_item = atomicAdd(p.counter, 1);
+  __shared__ int2 s_desc, s_next_desc;
+  if (threadIdx.x == 0) {
+    s_item = atomicAdd(p.counter, 1);
+    if (s_item < p.total) s_desc = p.items[s_item];
+  }
   __syncthreads();
   for (;;) {
     const int it = s_item;
     if (it >= p.total) return;
-    // claim the next item now; the atomic's latency overlaps this item's work
-    if (threadIdx.x == 0) s_next = atomicAdd(p.counter, 1);
-    const int2 d = p.items[it];
+    const int2 d = s_desc;
+    // claim the next item (and fetch its descriptor) now: the latency of the
+    // atomic and of the load overlaps this item's work
+    if (threadIdx.x == 0) {
+      const int nx = atomicAdd(p.counter, 1);
+      s_next = nx;
+      if (nx < p.total) s_next_desc = p.items[nx];
+    }
     const int s = d.x, stage = d.y >> 24, idx = d.y & 0xffffff;
     if (threadIdx.x == 0) {
       int ok = (stage != p.drop_stage);
@@ -162,7 +173,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batched_kernel(BatchParams<T
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) s_item = s_next;
+    if (threadIdx.x == 0) {
+      s_item = s_next;
+      s_desc = s_next_desc;
+    }
     __syncthreads();
   }
 }
@@ -185,10 +199,10 @@ size_t item_smem(int nx, int nz) {
     case 1024: z = zs(ZCfg<T, 1024, kBatchZWarps>{}, z_pipe_fits<T, 1024>()); break;
   }
   switch (nx) {
-    case 16: t = TSymCfg<T, 16, 1, kBatchThreads>::smem_bytes(); break;
-    case 32: t = TSymCfg<T, 32, 1, kBatchThreads>::smem_bytes(); break;
-    case 64: t = TSymCfg<T, 64, 1, kBatchThreads>::smem_bytes(); break;
-    case 128: t = TSymCfg<T, 128, 1, kBatchThreads>::smem_bytes(); break;
+    case 16: t = TCycCfg<T, 16, kBatchThreads>::smem_bytes(); break;
+    case 32: t = TCycCfg<T, 32, kBatchThreads>::smem_bytes(); break;
+    case 64: t = TCycCfg<T, 64, kBatchThreads>::smem_bytes(); break;
+    case 128: t = TCycCfg<T, 128, kBatchThreads>::smem_bytes(); break;
   }
   return z > t ? z : t;
 }
@@ -206,34 +220,56 @@ int z_cols(int nz) {
   return 0;
 }
 
-// the work lists of one handle set, built and timed on first use, kept by handles[0]
-struct BatchPlan {
-  int n = 0;
-  int dtype = 0;
-  pipe_handle* handles[kMaxBatch] = {};
+// One way of running a handle set: the solves in the persistent launch
+// ("members", with their work lists) and the solves left to their own
+// single-solve launches ("outside").
+struct BatchVariant {
+  std::vector<int> members;
+  std::vector<int> outside;
+  int n = 0;                 // members.size()
   void* solves = nullptr;    // SolveArgs<T>[n]
   int2* lists[3] = {nullptr, nullptr, nullptr};   // candidate work lists
   int2* items = nullptr;     // the chosen one
-  bool tuned = false;
   int2* need = nullptr;
   int2* per = nullptr;
   int* words = nullptr;      // done[2n], counter, status
   int total = 0;
   size_t smem = 0;
   int grid = 0;
-  int order = 0;                // chosen work-list order
+  int order = 0;
+};
+
+// Built and timed on the first call for a handle set, kept by handles[0].
+struct BatchPlan {
+  int n = 0;
+  int dtype = 0;
+  pipe_handle* handles[kMaxBatch] = {};
+  // variant k: the solves whose z spectrum is smaller than the k-th largest
+  // spectrum size in the set run persistent, the others outside (k = 0: all
+  // persistent; the last variant may have none persistent)
+  static constexpr int kMaxVar = 5;
+  BatchVariant var[kMaxVar];
+  int nvar = 0;
+  int chosen = 0;
+  int last = 0;              // variant of the last call (its status word is read back)
+  bool tuned = false;
   int drop_stage = -1;          // fault injection for the next launch only
   long long spin_limit = 1ll << 22;
 };
 
+void variant_release(BatchVariant& v) {
+  cudaFree(v.solves);
+  for (int k = 0; k < 3; ++k) cudaFree(v.lists[k]);
+  cudaFree(v.need);
+  cudaFree(v.per);
+  cudaFree(v.words);
+  v = BatchVariant();
+}
+
 void batch_release(pipe_handle* h) {
   if (!h || !h->batch) return;
   BatchPlan* b = static_cast<BatchPlan*>(h->batch);
-  cudaFree(b->solves);
-  for (int k = 0; k < 3; ++k) cudaFree(b->lists[k]);
-  cudaFree(b->need);
-  cudaFree(b->per);
-  cudaFree(b->words);
+  for (int k = 0; k < BatchPlan::kMaxVar; ++k) variant_release(b->var[k]);
   delete b;
   h->batch = nullptr;
 }
@@ -245,6 +281,7 @@ SolveArgs<float> batch_args<float>(pipe_handle* h) {
   SolveArgs<float> a{};
   a.work = static_cast<float2*>(h->work); a.green = h->green32;
   a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32; a.tw_t2 = h->tw_t2_32;
+  a.tw_t2c = h->tw_t2c_32;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
@@ -254,6 +291,7 @@ SolveArgs<double> batch_args<double>(pipe_handle* h) {
   SolveArgs<double> a{};
   a.work = static_cast<double2*>(h->work); a.green = h->green64;
   a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64; a.tw_t2 = h->tw_t2_64;
+  a.tw_t2c = h->tw_t2c_64;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
@@ -273,7 +311,10 @@ SolveArgs<double> batch_args<double>(pipe_handle* h) {
 //     stages; the small solves (pipelined among themselves) fill the gaps.
 // In every order an item appears after all items it waits for.
 template <typename T>
-int build_plan(pipe_handle* const* hs, int n, BatchPlan* b) {
+int build_variant(pipe_handle* const* all, BatchVariant* b) {
+  const int n = b->n;
+  std::vector<pipe_handle*> hs(n);
+  for (int s = 0; s < n; ++s) hs[s] = all[b->members[s]];
   std::vector<SolveArgs<T>> solves(n);
   std::vector<int2> need(n);
   std::vector<int2> per(n);
@@ -354,8 +395,12 @@ int build_plan(pipe_handle* const* hs, int n, BatchPlan* b) {
       cudaMemset(b->words, 0, sizeof(int) * (2 * n + 2)) != cudaSuccess)
     return PIPE_ECUDA;
   if (smem > kMaxSmem) return PIPE_EUNSUPPORTED;
-  if (cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-      cudaSuccess)
+  // the attribute belongs to the kernel, shared by every plan: only raise it
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, batched_kernel<T>) != cudaSuccess) return PIPE_ECUDA;
+  if (int(smem) > fa.maxDynamicSharedSizeBytes &&
+      cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+          cudaSuccess)
     return PIPE_ECUDA;
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -368,7 +413,8 @@ int build_plan(pipe_handle* const* hs, int n, BatchPlan* b) {
 }
 
 template <typename T>
-int launch_batch(BatchPlan* b, const void* const* rho, void* const* phi, cudaStream_t st) {
+int launch_variant(BatchVariant* b, const void* const* rho, void* const* phi, int drop_stage,
+                   long long spin_limit, cudaStream_t st) {
   BatchParams<T> p;
   p.solves = static_cast<const SolveArgs<T>*>(b->solves);
   p.items = b->items;
@@ -379,21 +425,64 @@ int launch_batch(BatchPlan* b, const void* const* rho, void* const* phi, cudaStr
   p.status = b->words + 2 * b->n + 1;
   p.total = b->total;
   p.n = b->n;
-  p.spin_limit = b->spin_limit;      // default 2^22 polls of >= 200 ns: about a second
-  p.drop_stage = b->drop_stage;
-  b->drop_stage = -1;
-  b->spin_limit = 1ll << 22;
+  p.spin_limit = spin_limit;         // default 2^22 polls of >= 200 ns: about a second
+  p.drop_stage = drop_stage;
   for (int s = 0; s < b->n; ++s) {
-    p.rho[s] = static_cast<const T*>(rho[s]);
-    p.phi[s] = static_cast<T*>(phi[s]);
+    p.rho[s] = static_cast<const T*>(rho[b->members[s]]);
+    p.phi[s] = static_cast<T*>(phi[b->members[s]]);
   }
   for (int s = b->n; s < kMaxBatch; ++s) {
     p.rho[s] = nullptr;
     p.phi[s] = nullptr;
   }
-  if (cudaMemsetAsync(b->words, 0, sizeof(int) * (2 * b->n + 2), st) != cudaSuccess) return PIPE_ECUDA;
-  batched_kernel<T><<<b->grid, kBatchThreads, b->smem, st>>>(p);
-  return cudaGetLastError() == cudaSuccess ? PIPE_OK : PIPE_ECUDA;
+  if (b->n > 0) {
+    if (cudaMemsetAsync(b->words, 0, sizeof(int) * (2 * b->n + 2), st) != cudaSuccess) return PIPE_ECUDA;
+    batched_kernel<T><<<b->grid, kBatchThreads, b->smem, st>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return PIPE_ECUDA;
+  }
+  return PIPE_OK;
+}
+
+// spectrum bytes of a solve (the "large" solves are those whose spectrum is a
+// sizeable part of L2; candidates for their own launches)
+static double spectrum_bytes(const pipe_handle* h) {
+  return double(h->grid.nx) * h->grid.ny * (h->grid.nz + 1) * (h->grid.dtype == PIPE_F64 ? 16 : 8);
+}
+
+template <typename T>
+static int build_plan(pipe_handle* const* hs, int n, BatchPlan* b) {
+  std::vector<double> sizes;
+  for (int s = 0; s < n; ++s) sizes.push_back(spectrum_bytes(hs[s]));
+  std::sort(sizes.begin(), sizes.end(), [](double x, double y) { return x > y; });
+  sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+  // cut-offs: none, then each distinct size from the largest down
+  const int ncut = std::min(int(sizes.size()) + 1, BatchPlan::kMaxVar);
+  for (int k = 0; k < ncut; ++k) {
+    BatchVariant& v = b->var[k];
+    for (int s = 0; s < n; ++s)
+      (k > 0 && spectrum_bytes(hs[s]) >= sizes[k - 1] ? v.outside : v.members).push_back(s);
+    v.n = int(v.members.size());
+    if (v.n > 0) {
+      const int st = build_variant<T>(hs, &v);
+      if (st != PIPE_OK) return st;
+    }
+    b->nvar = k + 1;
+  }
+  return PIPE_OK;
+}
+
+// one batched call with variant v: the persistent launch, then the solves
+// outside it, all on stream st
+static int run_variant(BatchPlan* b, int v, pipe_handle* const* hs, const void* const* rho,
+                       void* const* phi, cudaStream_t st) {
+  BatchVariant& x = b->var[v];
+  int r = b->dtype == PIPE_F64 ? launch_variant<double>(&x, rho, phi, b->drop_stage, b->spin_limit, st)
+                               : launch_variant<float>(&x, rho, phi, b->drop_stage, b->spin_limit, st);
+  for (size_t k = 0; r == PIPE_OK && k < x.outside.size(); ++k) {
+    const int s = x.outside[k];
+    r = handle_solve(hs[s], rho[s], phi[s], false, st);
+  }
+  return r;
 }
 
 }  // namespace pp
@@ -435,34 +524,41 @@ extern "C" int pipe_poisson_solve_batched(pipe_handle* const* handles, const voi
   }
   if (st == PIPE_OK) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    auto go = [&]() {
-      return b->dtype == PIPE_F64 ? launch_batch<double>(b, rho, phi, s) : launch_batch<float>(b, rho, phi, s);
-    };
     if (!b->tuned) {
-      // time each candidate work list once (the results are valid solves)
+      // time every (variant, work-list order) once after a warm-up run and
+      // keep the fastest; these runs are valid solves
       float best = 1e30f;
-      int pick = 0;
+      int pick_v = 0, pick_o = 0;
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
-      for (int k = 0; k < 3 && st == PIPE_OK; ++k) {
-        b->items = b->lists[k];
-        st = go();                                     // warm-up of this order
-        cudaEventRecord(e0, s);
-        if (st == PIPE_OK) st = go();
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (st == PIPE_OK && ms < best) { best = ms; pick = k; }
-      }
+      for (int v = 0; v < b->nvar && st == PIPE_OK; ++v)
+        for (int k = 0; k < (b->var[v].n > 0 ? 3 : 1) && st == PIPE_OK; ++k) {
+          b->var[v].items = b->var[v].lists[k];
+          st = run_variant(b, v, handles, rho, phi, s);
+          cudaEventRecord(e0, s);
+          if (st == PIPE_OK) st = run_variant(b, v, handles, rho, phi, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (st == PIPE_OK && ms < best) { best = ms; pick_v = v; pick_o = k; }
+        }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      b->items = b->lists[pick];
-      b->order = pick;
+      for (int v = 0; v < b->nvar; ++v) {
+        b->var[v].order = (v == pick_v) ? pick_o : 0;
+        b->var[v].items = b->var[v].lists[b->var[v].order];
+      }
+      b->chosen = pick_v;
       b->tuned = true;
     }
-    if (st == PIPE_OK) st = go();
+    // an injected fault is meant for the persistent launch: run every solve there
+    const int v = b->drop_stage >= 0 ? 0 : b->chosen;
+    if (st == PIPE_OK) st = run_variant(b, v, handles, rho, phi, s);
+    b->last = v;
+    b->drop_stage = -1;
+    b->spin_limit = 1ll << 22;
   }
   if (cur >= 0 && cur != handles[0]->device) cudaSetDevice(cur);
   return st;
@@ -471,9 +567,11 @@ extern "C" int pipe_poisson_solve_batched(pipe_handle* const* handles, const voi
 extern "C" int pipe_batch_status(pipe_handle* const* handles, int n) {
   if (!handles || n < 1 || !handles[0]) return PIPE_EINVAL;
   BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
-  if (!b) return PIPE_EINVAL;
+  if (!b || b->n != n) return PIPE_EINVAL;
+  const BatchVariant& x = b->var[b->last];
+  if (x.n == 0) return PIPE_OK;
   int status = PIPE_OK;
-  if (cudaMemcpy(&status, b->words + 2 * b->n + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaMemcpy(&status, x.words + 2 * x.n + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return PIPE_ECUDA;
   return status;
 }
@@ -483,10 +581,36 @@ extern "C" int pipe_batch_inject_fault(pipe_handle* const* handles, int n, int d
   if (!handles || n < 1 || !handles[0] || drop_stage < 0 || drop_stage > 2 || spin_limit < 0)
     return PIPE_EINVAL;
   BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
-  if (!b || b->n != n) return PIPE_EINVAL;
+  if (!b || b->n != n || !b->tuned) return PIPE_EINVAL;
   for (int s = 0; s < n; ++s)
     if (b->handles[s] != handles[s]) return PIPE_EINVAL;
   b->drop_stage = drop_stage;
   b->spin_limit = spin_limit;
+  return PIPE_OK;
+}
+
+extern "C" int pipe_batch_plan_info(pipe_handle* const* handles, int n, int* persistent, int* order) {
+  if (!handles || n < 1 || !handles[0] || !persistent || !order) return PIPE_EINVAL;
+  BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
+  if (!b || b->n != n || !b->tuned) return PIPE_EINVAL;
+  for (int s = 0; s < n; ++s)
+    if (b->handles[s] != handles[s]) return PIPE_EINVAL;
+  *persistent = b->var[b->chosen].n;
+  *order = b->var[b->chosen].order;
+  return PIPE_OK;
+}
+
+extern "C" int pipe_batch_select(pipe_handle* const* handles, int n, int variant, int order) {
+  if (!handles || n < 1 || !handles[0]) return PIPE_EINVAL;
+  BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
+  if (!b || b->n != n || !b->tuned) return PIPE_EINVAL;
+  for (int s = 0; s < n; ++s)
+    if (b->handles[s] != handles[s]) return PIPE_EINVAL;
+  if (variant < 0 || variant >= b->nvar || order < 0 || order > 2) return PIPE_EINVAL;
+  BatchVariant& v = b->var[variant];
+  if (v.n == 0 && order != 0) return PIPE_EINVAL;
+  v.order = order;
+  if (v.n > 0) v.items = v.lists[order];
+  b->chosen = variant;
   return PIPE_OK;
 }

@@ -371,7 +371,8 @@ template <int L> struct GroupShape {
 };
 
 // v: E values in cyclic layout; scratch: SCRATCH complex in shared memory (per
-// group); tw: L entries, tw[k1*G + t] = e^{-2 pi i t k1 / L}; t: lane in group.
+// group); tw: L entries in GLOBAL memory (read with __ldg),
+// tw[k1*G + t] = e^{-2 pi i t k1 / L}; t: lane in group.
 // All lanes of the warp must call this together (it uses __syncwarp).
 template <int L, bool INV, typename V>
 __device__ __forceinline__ void group_fft(V (&v)[GroupShape<L>::E], V* scratch, const V* __restrict__ tw,

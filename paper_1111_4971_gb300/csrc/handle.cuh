@@ -28,8 +28,10 @@ struct pipe_handle {
   void* work = nullptr;  // (nz+1)*nx*ny complex of the dtype
   float2* tab32 = nullptr;
   double2* tab64 = nullptr;
-  float2 *tw_t32 = nullptr, *w2_t32 = nullptr, *tw_z32 = nullptr, *w2_z32 = nullptr, *tw_t2_32 = nullptr;
-  double2 *tw_t64 = nullptr, *w2_t64 = nullptr, *tw_z64 = nullptr, *w2_z64 = nullptr, *tw_t2_64 = nullptr;
+  float2 *tw_t32 = nullptr, *w2_t32 = nullptr, *tw_z32 = nullptr, *w2_z32 = nullptr, *tw_t2_32 = nullptr,
+         *tw_t2c_32 = nullptr;
+  double2 *tw_t64 = nullptr, *w2_t64 = nullptr, *tw_z64 = nullptr, *w2_z64 = nullptr, *tw_t2_64 = nullptr,
+          *tw_t2c_64 = nullptr;
   void* stage_rho = nullptr;   // device staging for pipe_poisson_solve_host
   void* stage_phi = nullptr;
   pp::Plan plan{8, 0, 1, 256};

@@ -58,6 +58,7 @@ pp::SolveArgs<float> noalloc_args<float>(pipe_handle* h, const void* rho, void* 
   a.rho = static_cast<const float*>(rho); a.phi = static_cast<float*>(phi);
   a.work = static_cast<float2*>(work); a.green = h->green32;
   a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32; a.tw_t2 = h->tw_t2_32;
+  a.tw_t2c = h->tw_t2c_32;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
@@ -68,6 +69,7 @@ pp::SolveArgs<double> noalloc_args<double>(pipe_handle* h, const void* rho, void
   a.rho = static_cast<const double*>(rho); a.phi = static_cast<double*>(phi);
   a.work = static_cast<double2*>(work); a.green = h->green64;
   a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64; a.tw_t2 = h->tw_t2_64;
+  a.tw_t2c = h->tw_t2c_64;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;

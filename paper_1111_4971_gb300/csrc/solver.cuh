@@ -20,6 +20,7 @@ struct SolveArgs {
   const C2<T>* tw_t;
   const C2<T>* w2_t;
   const C2<T>* tw_t2;   // paired-layout twiddles of the 2n-point transverse FFTs
+  const C2<T>* tw_t2c;  // cyclic-layout twiddles of the 2n-point transverse FFTs
   const C2<T>* tw_z;
   const C2<T>* w2_z;
   int nx, ny, nz;

@@ -40,8 +40,34 @@ static cudaError_t tslaunch(const SolveArgs<T>& a, cudaStream_t st) {
   }
 }
 
+// the cyclic-layout variant: one CTA of 512 threads per plane
+template <typename T, int N, bool ADJ>
+__global__ void __launch_bounds__(512, 1) transverse_cyc_kernel(SolveArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tsym_cyc_plane<T, N, 512, ADJ>(a, blockIdx.x, smem_raw);
+}
+
+template <typename T, int N, bool ADJ>
+static cudaError_t tclaunch(const SolveArgs<T>& a, cudaStream_t st) {
+  using Cfg = TCycCfg<T, N, 512>;
+  if constexpr (Cfg::smem_bytes() > kMaxSmem) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    const size_t smem = Cfg::smem_bytes();
+    void (*kern)(SolveArgs<T>) = transverse_cyc_kernel<T, N, ADJ>;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<a.nz + 1, 512, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+}
+
 template <typename T, int N>
 static cudaError_t tslaunch2(bool adjoint, int hb, int threads, const SolveArgs<T>& a, cudaStream_t st) {
+  if (hb == 1 && threads == 512)            // cyclic-layout variant, 16 warps
+    return adjoint ? tclaunch<T, N, true>(a, st) : tclaunch<T, N, false>(a, st);
 #define PP_TS_CASE(HH, TT)                                                           \
   if (hb == HH && threads == TT)                                                     \
     return adjoint ? tslaunch<T, N, HH, TT, true>(a, st) : tslaunch<T, N, HH, TT, false>(a, st);

@@ -23,11 +23,12 @@ namespace pp {
 Plan default_plan(int n, int nz, bool f64) {
   Plan p;
   p.z_warps = (!f64 && nz >= 512) ? 16 : 8;
-  // autotuned on GB300 for 128^2 x 1024: FP32 (8 warps, 1 CTA per plane),
-  // FP64 (8 warps, 2-CTA clusters of 128 threads)
+  // autotuned on GB300 at 128^2 x 1024: FP32 one 512-thread CTA per plane
+  // (cyclic-layout FFTs); FP64 2-CTA clusters of 128 threads
   p.z_warps = 8;
   p.z_pipe = 0;
-  if (n < 128 || !f64) { p.t_h = 1; p.t_threads = 256; }
+  if (!f64) { p.t_h = 1; p.t_threads = 512; }
+  else if (n < 128) { p.t_h = 1; p.t_threads = 256; }
   else { p.t_h = 2; p.t_threads = 128; }
   return p;
 }
@@ -84,6 +85,7 @@ SolveArgs<float> args_for<float>(pipe_handle* h, void* rho, void* phi) {
   a.work = static_cast<float2*>(h->work); a.green = h->green32;
   a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32;
   a.tw_t2 = h->tw_t2_32;
+  a.tw_t2c = h->tw_t2c_32;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
@@ -95,6 +97,7 @@ SolveArgs<double> args_for<double>(pipe_handle* h, void* rho, void* phi) {
   a.work = static_cast<double2*>(h->work); a.green = h->green64;
   a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64;
   a.tw_t2 = h->tw_t2_64;
+  a.tw_t2c = h->tw_t2c_64;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
@@ -140,7 +143,7 @@ int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
       if (ms > 0 && ms < bz) { bz = ms; best.z_warps = zw; best.z_pipe = zp; }
     }
   if (h->images) {
-    const int shapes[6][2] = {{1, 128}, {1, 256}, {2, 128}, {2, 256}, {4, 128}, {4, 256}};
+    const int shapes[7][2] = {{1, 128}, {1, 256}, {1, 512}, {2, 128}, {2, 256}, {4, 128}, {4, 256}};
     for (auto& sh : shapes) {
       float ms = time_ms([&] { return launch_transverse_sym<T>(false, sh[0], sh[1], a, st); }, st, reps);
       if (ms > 0 && ms < bt) { bt = ms; best.t_h = sh[0]; best.t_threads = sh[1]; }

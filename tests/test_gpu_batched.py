@@ -25,22 +25,43 @@ def make_set(count, seed=4, dtype=torch.float32):
     solvers, rhos = [], []
     for it in items:
         s = PipeSolver(it["geom"], it["grid"], igf=True, dtype=dtype)
-        s.set_plan(z_warps=8, z_pipe=1, t_h=1, t_threads=256)   # the shape the batched kernel runs
+        s.set_plan(z_warps=16, z_pipe=0, t_h=1, t_threads=512)   # the transverse shape of the batched kernel
         solvers.append(s)
         rhos.append(torch.tensor(it["rho"], dtype=dtype, device="cuda"))
     return items, solvers, rhos
 
 
 def test_batched_equals_loop_bitwise_and_oracle():
-    from paper_1111_4971_gb300 import batch_status, solve_batched
+    from paper_1111_4971_gb300 import batch_plan_info, batch_select, batch_status, solve_batched
     items, solvers, rhos = make_set(10)
     phis_b = [s.empty() for s in solvers]
-    solve_batched(solvers, rhos, phis_b)
+    solve_batched(solvers, rhos, phis_b)          # tunes the split and the order
     torch.cuda.synchronize()
     assert batch_status(solvers) == 0
+    k, order = batch_plan_info(solvers)
+    assert 0 <= k <= 10 and order in (0, 1, 2)
+    loop = []
     for s, r, pb in zip(solvers, rhos, phis_b):
-        pl = s.solve(r)
+        loop.append(s.solve(r))
         torch.cuda.synchronize()
+        assert torch.equal(loop[-1], pb)
+    # every solve in the persistent launch, each work-list order
+    for order in (0, 1, 2):
+        batch_select(solvers, 0, order)
+        assert batch_plan_info(solvers) == (10, order)
+        phis = [s.empty().fill_(7.0) for s in solvers]
+        solve_batched(solvers, rhos, phis)
+        torch.cuda.synchronize()
+        assert batch_status(solvers) == 0
+        for pl, pb in zip(loop, phis):
+            assert torch.equal(pl, pb)
+    # the largest size class left to single-solve launches
+    batch_select(solvers, 1, 0)
+    assert batch_plan_info(solvers)[0] < 10
+    phis = [s.empty().fill_(7.0) for s in solvers]
+    solve_batched(solvers, rhos, phis)
+    torch.cuda.synchronize()
+    for pl, pb in zip(loop, phis):
         assert torch.equal(pl, pb)
     # the smallest solves against the oracle
     for it, pb in zip(items, phis_b):
@@ -57,7 +78,7 @@ def test_batched_fp64_small_sizes():
     solvers, rhos, wants = [], [], []
     for k, (g, gr) in enumerate(cases):
         s = PipeSolver(g, gr, igf=True, dtype=torch.float64)
-        s.set_plan(z_warps=8, z_pipe=1, t_h=1, t_threads=256)
+        s.set_plan(z_warps=8, z_pipe=0, t_h=1, t_threads=512)
         rho = random_density(gr.shape, 30 + k)
         solvers.append(s)
         rhos.append(torch.tensor(rho, dtype=torch.float64, device="cuda"))
