@@ -40,7 +40,7 @@ KERNEL_SOURCES = {
     "z_inverse": ["zfft_impl.cuh", "zfft.cu", "fft_common.cuh", "solver.cuh"],
 }
 PROFILE_FILES = {
-    "transverse": "transverse_sym_pipe128x128x1024_igf_f32.md",
+    "transverse": "transverse_cyc_pipe128x128x1024_igf_f32.md",
     "z_forward": "zfft_pipe128x128x1024_igf_f32.md",
     "z_inverse": "zfft_pipe128x128x1024_igf_f32.md",
 }
@@ -213,12 +213,13 @@ def run_reference(args):
 
 
 def bench_batched(args, count=96):
-    """96 independent IGF solves on mixed grids / aspect ratios: one persistent
-    launch replayed from a CUDA graph, against a loop of single solves."""
+    """96 independent IGF solves on mixed grids / aspect ratios: the batched
+    call (persistent launch plus the single-solve launches its tuner leaves
+    outside) replayed from a CUDA graph, against a loop of single solves."""
     import torch
 
     from inputs import bunches
-    from paper_1111_4971_gb300 import PipeSolver, batch_status, solve_batched
+    from paper_1111_4971_gb300 import PipeSolver, batch_plan_info, batch_status, solve_batched
     items = bunches.workload_batched_96(count=count)
     solvers, rhos = [], []
     for it in items:
@@ -253,10 +254,13 @@ def bench_batched(args, count=96):
             solve_batched(solvers, rhos, phis, stream=stream)
         batch_ms = timed(g.replay)
     ok = batch_status(solvers) == 0
+    persistent, order = batch_plan_info(solvers)
     return {"solves": count, "grids": grids, "batched_ms": batch_ms, "loop_ms": loop_ms,
             "batched_solves_per_s": count / (batch_ms * 1e-3),
             "loop_solves_per_s": count / (loop_ms * 1e-3), "speedup": loop_ms / batch_ms,
-            "status_ok": ok, "launches_per_batch": 1}
+            "status_ok": ok, "persistent_solves": persistent,
+            "order": ["stage-major", "pipelined", "L2-local"][order],
+            "launches_per_batch": (1 if persistent else 0) + 3 * (count - persistent)}
 
 
 def run_ours(args):

@@ -150,8 +150,8 @@ int pipe_poisson_solve_host(pipe_handle* h, const void* rho_host, void* phi_host
  * synchronises the stream.  Later calls with the same set reuse the
  * choice and are capturable in a CUDA graph.  Results equal those of
  * pipe_poisson_solve up to rounding, and bitwise for FP32 handles whose plan is
- * z_warps = 16, z_pipe = 0, t_h = 1, t_threads = 512 (the persistent kernel's
- * shapes).
+ * z_warps = 16, z_pipe = 0, t_h = 1, t_threads = 512, and t_kind = 1 on
+ * cell-centred meshes, 0 on others (the persistent kernel's shapes).
  * Errors: PIPE_EINVAL (n < 1, null arrays), PIPE_EUNSUPPORTED (mixed dtypes
  * or devices), PIPE_ENOMEM, PIPE_ECUDA. */
 int pipe_poisson_solve_batched(pipe_handle* const* handles, const void* const* rho,
@@ -215,11 +215,17 @@ int pipe_autotune(pipe_handle* h, void* stream);
  * the z transforms), z_pipe in {0, 1} (1: each z CTA walks several tiles and
  * streams the next tile's input while transforming the current one), t_h in
  * {1, 2, 4} (the transverse stage runs t_h CTAs per kz plane, each holding
- * nx/t_h rows), t_threads in {128, 256, 512}.  pipe_set_plan returns
- * PIPE_EINVAL for values outside those sets; a variant that does not fit the
- * device (shared memory) makes the next solve fail with PIPE_ECUDA. */
-int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h, int* t_threads);
-int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads);
+ * nx/t_h rows), t_threads in {128, 256, 512}, t_kind in {0, 1}: 0 computes
+ * each transverse line with the padded 2n-point transforms of Eq. 10 (any
+ * supported mesh); 1 computes the same combinations with n-point transforms,
+ * for cell-centred meshes only (2*x0/hx == 2*y0/hy == 1), t_h == 1 and an
+ * nx*ny complex plane of at most 200 KB (FP32 up to 128^2, FP64 up to 64^2).
+ * pipe_set_plan returns PIPE_EINVAL for values outside those sets and
+ * PIPE_EUNSUPPORTED for t_kind 1 on other meshes; a variant that does not fit
+ * the device (shared memory) makes the next solve fail with PIPE_ECUDA.
+ * The free-space (Hockney) handle ignores t_kind. */
+int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h, int* t_threads, int* t_kind);
+int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads, int t_kind);
 
 /* Cloud-in-cell deposit of n macroparticles (positions xyz[n][3], FP64 or FP32
  * per the handle's dtype, charge q each) onto the handle's mesh nodes:

@@ -135,14 +135,15 @@ class PipeSolver:
 
     @property
     def plan(self):
-        z, zp, h, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        z, zp, h, t, k = (ctypes.c_int() for _ in range(5))
         check(self.lib.pipe_get_plan(self.handle, ctypes.byref(z), ctypes.byref(zp), ctypes.byref(h),
-                                     ctypes.byref(t)), "pipe_get_plan")
-        return {"z_warps": z.value, "z_pipe": zp.value, "t_h": h.value, "t_threads": t.value}
+                                     ctypes.byref(t), ctypes.byref(k)), "pipe_get_plan")
+        return {"z_warps": z.value, "z_pipe": zp.value, "t_h": h.value, "t_threads": t.value,
+                "t_kind": k.value}
 
-    def set_plan(self, z_warps=8, z_pipe=1, t_h=1, t_threads=256):
-        check(self.lib.pipe_set_plan(self.handle, int(z_warps), int(z_pipe), int(t_h), int(t_threads)),
-              "pipe_set_plan")
+    def set_plan(self, z_warps=8, z_pipe=1, t_h=1, t_threads=256, t_kind=0):
+        check(self.lib.pipe_set_plan(self.handle, int(z_warps), int(z_pipe), int(t_h), int(t_threads),
+                                     int(t_kind)), "pipe_set_plan")
 
     def cic_deposit(self, xyz: torch.Tensor, charge: float, out: torch.Tensor | None = None,
                     stream=None):

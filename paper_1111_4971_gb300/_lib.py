@@ -54,8 +54,9 @@ SIGNATURES = {
     "pipe_stage_transverse": (c_int, [H, c_void_p, c_int, c_void_p]),
     "pipe_stage_z_inverse": (c_int, [H, c_void_p, c_void_p, c_int, c_void_p]),
     "pipe_autotune": (c_int, [H, c_void_p]),
-    "pipe_get_plan": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
-    "pipe_set_plan": (c_int, [H, c_int, c_int, c_int, c_int]),
+    "pipe_get_plan": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                              POINTER(c_int)]),
+    "pipe_set_plan": (c_int, [H, c_int, c_int, c_int, c_int, c_int]),
     "pipe_cic_deposit": (c_int, [H, c_void_p, c_int64, c_double, c_void_p, c_void_p]),
     "pipe_cic_gather_grad": (c_int, [H, c_void_p, c_int64, c_double, c_void_p, c_void_p, c_void_p]),
     "pipe_green_destroy": (None, [H]),

@@ -143,7 +143,8 @@ SolveArgs<double> make_args<double>(pipe_handle* h, const void* rho, void* phi, 
 
 template <typename T>
 cudaError_t transverse_stage(pipe_handle* h, bool adjoint, const SolveArgs<T>& a, cudaStream_t st) {
-  if (h->images) return launch_transverse_sym<T>(adjoint, h->plan.t_h, h->plan.t_threads, a, st);
+  if (h->images)
+    return launch_transverse_sym<T>(adjoint, h->plan.t_kind, h->plan.t_h, h->plan.t_threads, a, st);
   return launch_transverse<T>(adjoint, h->free_plan.t_h, h->free_plan.t_threads, a, st);
 }
 
@@ -248,7 +249,7 @@ int pipe_green_setup(const pipe_geometry* geom, const pipe_grid* grid, int igf, 
   h->sx = sx;
   h->sy = sy;
   h->images = 1;
-  h->plan = default_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
+  h->plan = default_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64, sx == 1 && sy == 1);
   h->free_plan = default_free_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
   if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
   GreenSpec s;
@@ -278,7 +279,7 @@ int pipe_free_space_setup(const pipe_grid* grid, double self_value, pipe_handle*
   h->kind = 2;
   h->sx = h->sy = 0;
   h->images = 0;
-  h->plan = default_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
+  h->plan = default_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64, false);
   h->free_plan = default_free_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
   if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
   if (!(self_value > 0)) self_value = 1.0 / std::fmin(grid->hx, std::fmin(grid->hy, grid->hz));

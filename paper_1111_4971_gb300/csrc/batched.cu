@@ -27,6 +27,7 @@
 
 #include "../../include/pipe_poisson.h"
 #include "handle.cuh"
+#include "tdst_impl.cuh"
 #include "tsym_impl.cuh"
 #include "zfft_impl.cuh"
 
@@ -91,6 +92,12 @@ __device__ __noinline__ void t_item(const SolveArgs<T>& a, int item, int per, un
     const int kz = item * per + k;
     if (kz > a.nz) break;
     if (k) __syncthreads();
+    if constexpr (TDstCfg<T, N, kBatchThreads>::smem_bytes() <= kMaxSmem) {
+      if (a.sx == 1 && a.sy == 1) {                // cell-centred: the n-point routine
+        tdst_plane<T, N, kBatchThreads, false>(a, kz, smem);
+        continue;
+      }
+    }
     tsym_cyc_plane<T, N, kBatchThreads, false>(a, kz, smem);
   }
 }
@@ -198,11 +205,17 @@ size_t item_smem(int nx, int nz) {
     case 512: z = zs(ZCfg<T, 512, kBatchZWarps>{}, z_pipe_fits<T, 512>()); break;
     case 1024: z = zs(ZCfg<T, 1024, kBatchZWarps>{}, z_pipe_fits<T, 1024>()); break;
   }
+  auto ts = [](auto cyc, auto dst) {
+    using C = decltype(cyc);
+    using D = decltype(dst);
+    const size_t d = D::smem_bytes() <= kMaxSmem ? D::smem_bytes() : 0;
+    return C::smem_bytes() > d ? C::smem_bytes() : d;
+  };
   switch (nx) {
-    case 16: t = TCycCfg<T, 16, kBatchThreads>::smem_bytes(); break;
-    case 32: t = TCycCfg<T, 32, kBatchThreads>::smem_bytes(); break;
-    case 64: t = TCycCfg<T, 64, kBatchThreads>::smem_bytes(); break;
-    case 128: t = TCycCfg<T, 128, kBatchThreads>::smem_bytes(); break;
+    case 16: t = ts(TCycCfg<T, 16, kBatchThreads>{}, TDstCfg<T, 16, kBatchThreads>{}); break;
+    case 32: t = ts(TCycCfg<T, 32, kBatchThreads>{}, TDstCfg<T, 32, kBatchThreads>{}); break;
+    case 64: t = ts(TCycCfg<T, 64, kBatchThreads>{}, TDstCfg<T, 64, kBatchThreads>{}); break;
+    case 128: t = ts(TCycCfg<T, 128, kBatchThreads>{}, TDstCfg<T, 128, kBatchThreads>{}); break;
   }
   return z > t ? z : t;
 }

@@ -13,6 +13,8 @@ struct Plan {
   int z_pipe;      // 1: pipelined multi-tile z kernels, 0: one tile per CTA
   int t_h;         // transverse stage: row blocks per kz plane (CTAs per cluster)
   int t_threads;   // threads per transverse CTA
+  int t_kind = 0;  // 0: 2N-point transverse routines (any mesh), 1: N-point routine
+                   //    (cell-centred meshes, s = 2 x0 / h = 1 on both axes)
 };
 }  // namespace pp
 
@@ -40,7 +42,7 @@ struct pipe_handle {
 };
 
 namespace pp {
-Plan default_plan(int n, int nz, bool f64);        // pipe operator
+Plan default_plan(int n, int nz, bool f64, bool cell_centred);   // pipe operator
 Plan default_free_plan(int n, int nz, bool f64);   // free-space stage
 void batch_release(pipe_handle* h);
 int handle_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStream_t st);

@@ -82,7 +82,7 @@ int noalloc_run(pipe_handle* h, const void* rho, void* phi, void* work, cudaStre
   const pp::Plan& p = h->plan;
   cudaError_t e = pp::launch_z<T>(true, p.z_warps, p.z_pipe, false, a, st);
   if (e == cudaSuccess)
-    e = h->images ? pp::launch_transverse_sym<T>(false, p.t_h, p.t_threads, a, st)
+    e = h->images ? pp::launch_transverse_sym<T>(false, p.t_kind, p.t_h, p.t_threads, a, st)
                   : pp::launch_transverse<T>(false, h->free_plan.t_h, h->free_plan.t_threads, a, st);
   if (e == cudaSuccess) e = pp::launch_z<T>(false, p.z_warps, p.z_pipe, false, a, st);
   return e == cudaSuccess ? PIPE_OK : PIPE_ECUDA;

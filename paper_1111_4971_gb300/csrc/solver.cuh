@@ -108,7 +108,7 @@ cudaError_t launch_z(bool forward, int warps, int pipe, bool conj, const SolveAr
 template <typename T>
 cudaError_t launch_transverse(bool adjoint, int h, int threads, const SolveArgs<T>& a, cudaStream_t st);
 template <typename T>
-cudaError_t launch_transverse_sym(bool adjoint, int hb, int threads, const SolveArgs<T>& a,
+cudaError_t launch_transverse_sym(bool adjoint, int kind, int hb, int threads, const SolveArgs<T>& a,
                                   cudaStream_t st);
 
 }  // namespace pp

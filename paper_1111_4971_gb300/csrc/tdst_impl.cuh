@@ -1,0 +1,278 @@
+// Pipe-operator transverse stage for cell-centred meshes (x0 = hx/2,
+// y0 = hy/2, mesh spanning the pipe): the same operator as tsym_impl.cuh, with
+// every padded 2N-point transform replaced by an N-point one.
+//
+// Why this is the same operator.  Along one transverse axis the stage forms,
+// from the N physical samples x_j of a line, the combination
+//     U(q) = Y(q) - w^{-s q} Y(-q),   q = 1..N,
+// where Y is the 2N-point transform of the zero-padded line, w = e^{-i pi/N}
+// (conjugated for the adjoint) and s = 2 x0 / h is the image offset of the
+// correlation terms of Eq. 10 (the reflections R_t).  For s = 1, U is the
+// 2N-point transform of the antisymmetric extension z_j = x_j,
+// z_{2N-1-j} = -x_j.  Splitting z into even and odd samples and using the
+// antisymmetry turns the odd half into the even half reversed, so with
+//     v_n = z_{2n}  (x_{2n} for 2n < N, -x_{2N-1-2n} otherwise),
+//     V = N-point transform of v,
+// one has U(q) = V(q) - w^{-q} V(N-q) for q = 1..N-1 and U(N) = 2 V(0).
+// The inverse direction is the transpose: a spectrum with P(-q) = -w^q P(q)
+// (what the Green product of Eq. 10 leaves, the table being even in q) has
+// as its 2N-point inverse transform a sequence antisymmetric in the same
+// sense, whose even samples are the N-point inverse transform of
+//     V'(q) = P(q) + w^{-q} P(N-q),  V'(0) = P(N),
+// and whose odd samples 2n+1 are minus the even sample 2(N-1-n).  Each line
+// therefore costs one N-point transform plus a mirror combination of the
+// pairs (q, N-q), instead of a 2N-point transform with half its inputs zero.
+//
+// Layout and schedule are those of the cyclic 2N-point routine: one CTA per
+// kz plane, lanes of a group of G hold elements q = t + G e; pass 1 transforms
+// the N rows along y into the ky = 1..N columns of a shared-memory buffer,
+// pass 2 transforms each column along x, multiplies by the Green octant,
+// transforms back and stores it in place, pass 3 transforms the rows back.
+#pragma once
+
+#include "fft_common.cuh"
+#include "solver.cuh"
+
+namespace pp {
+
+template <typename T, int N, int THREADS>
+struct TDstCfg {
+  using S = GroupShape<N>;
+  static constexpr int G = S::G;
+  static constexpr int E = S::E;
+  static constexpr int LD = N;
+  static constexpr int SWM = (N < 16 ? N : 16) - 1;
+  static constexpr int YBUF = N * LD;
+  static constexpr int GROUPS = THREADS / G;
+  static constexpr size_t smem_bytes() {
+    return sizeof(C2<T>) * (size_t(YBUF) + size_t(2 * N) + size_t(GROUPS) * S::SSTRIDE);
+  }
+};
+
+// a + w * b
+template <typename V>
+__device__ __forceinline__ V cfma_(V a, V w, V b) {
+  return mk<V>(a.x + (w.x * b.x - w.y * b.y), a.y + (w.x * b.y + w.y * b.x));
+}
+
+template <typename T, int N, int THREADS, bool ADJ>
+struct TDst {
+  using Cfg = TDstCfg<T, N, THREADS>;
+  using V = C2<T>;
+  static constexpr int G = Cfg::G, E = Cfg::E, H = E / 2;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int GPW = 32 / G;
+  static constexpr int GPC = WARPS * GPW;                      // lines in flight per CTA
+  static constexpr bool INV1 = ADJ, INV2 = !ADJ;
+  static constexpr int MASK = 2 * N - 1;
+  static constexpr int SGN = ADJ ? 1 : -1;                     // w^{-q} = sw2[(SGN q) mod 2N]
+  // with registers to spare (at most 256 threads), the next rows' loads are
+  // issued before the current rows are transformed
+  static constexpr bool PREFETCH = THREADS <= 256;
+
+  V* ybuf;
+  V* sw2;                                                      // 2N phases w_{2N}^j
+  V* scratch;
+  const V* tw;                // N-point twiddles, read by group_fft from global memory
+  int lane, t, line;
+
+  __device__ __forceinline__ TDst(const SolveArgs<T>& a, unsigned char* smem_raw) {
+    ybuf = reinterpret_cast<V*>(smem_raw);
+    sw2 = ybuf + Cfg::YBUF;
+    scratch = sw2 + 2 * N + (threadIdx.x / G) * GroupShape<N>::SSTRIDE;
+    tw = a.tw_t;
+    lane = threadIdx.x & 31;
+    t = lane % G;
+    line = lane / G + GPW * (threadIdx.x >> 5);                // groups of a warp: adjacent lines
+  }
+
+  __device__ static __forceinline__ int tile(int ky, int il) {
+    return (ky - 1) * Cfg::LD + (il ^ ((ky - 1) & Cfg::SWM));
+  }
+
+  // the even/odd-split samples v_n of row il (row 0 stands in past the end)
+  __device__ __forceinline__ void load_row(const V* plane, int il, V (&v)[E]) const {
+    const V* row = plane + size_t(il < N ? il : 0) * N;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int n = t + G * e;
+      if (e < H) {
+        v[e] = row[2 * n];
+      } else {
+        const V x = row[2 * N - 1 - 2 * n];
+        v[e] = mk<V>(-x.x, -x.y);
+      }
+    }
+  }
+
+  // the phase table; the caller synchronises before the first plane
+  __device__ __forceinline__ void load_tables(const SolveArgs<T>& a) {
+    for (int i = threadIdx.x; i < 2 * N; i += THREADS) sw2[i] = a.w2_t[i];
+  }
+
+  // Plane kz in place.  On entry v holds this plane's row `line` (load_row);
+  // on return, if next != nullptr, it holds row `line` of the plane at next.
+  // Ends with the plane's stores issued; the caller synchronises before
+  // another plane reuses the buffers.
+  __device__ __forceinline__ void plane(const SolveArgs<T>& a, int kz, V (&v)[E], const V* next) {
+    V* pl = a.work + size_t(kz) * N * N;
+
+    // pass 1: rows i, along y -> ybuf[ky][i], ky = 1..N
+#pragma unroll 1
+    for (int r0 = 0; r0 < N; r0 += GPC) {
+      const int il = r0 + line;
+      V nxt[PREFETCH ? E : 1];
+      if constexpr (PREFETCH) {
+        if (r0 + GPC < N) load_row(pl, r0 + GPC + line, nxt);
+      } else {
+        if (r0 > 0) load_row(pl, il, v);
+      }
+      group_fft<N, INV1>(v, scratch, tw, t);                   // V(q)
+      V m[E];
+      mirror_fetch<N>(v, m, t, 0, lane - t);                   // V(N-q)
+      if (il < N) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int q = t + G * e;
+          if (q == 0) ybuf[tile(N, il)] = mk<V>(v[e].x + v[e].x, v[e].y + v[e].y);
+          else ybuf[tile(q, il)] = cfms(v[e], sw2[(SGN * q) & MASK], m[e]);
+        }
+      }
+      if constexpr (PREFETCH) {
+        if (r0 + GPC < N) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) v[e] = nxt[e];
+        }
+      }
+    }
+    __syncthreads();
+
+    // pass 2: columns ky = 1..N, along x, Green product, back along x
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += GPC) {
+      const int cl = c0 + line;
+      const bool act = cl < N;
+      const int ky = 1 + (act ? cl : 0);
+      V u[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int n = t + G * e;
+        if (e < H) {
+          u[e] = ybuf[tile(ky, 2 * n)];
+        } else {
+          const V x = ybuf[tile(ky, 2 * N - 1 - 2 * n)];
+          u[e] = mk<V>(-x.x, -x.y);
+        }
+      }
+      const T* grow = a.green + (size_t(kz) * (N + 1) + ky) * (N + 1);
+      T g[E];                                   // Green row: before the transform if registers allow
+      auto load_g = [&] {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int kx = t + G * e;
+          g[e] = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
+        }
+      };
+      if constexpr (PREFETCH) load_g();
+      group_fft<N, INV1>(u, scratch, tw, t);                   // V(kx)
+      if constexpr (!PREFETCH) load_g();
+      V m[E];
+      mirror_fetch<N>(u, m, t, 0, lane - t);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int kx = t + G * e;
+        // slot 0 carries kx = N: U(N) = 2 V(0)
+        const V w = (kx == 0) ? mk<V>(u[e].x + u[e].x, u[e].y + u[e].y)
+                              : cfms(u[e], sw2[(SGN * kx) & MASK], m[e]);
+        u[e] = cscale(w, g[e]);                                // P(kx)
+      }
+      mirror_fetch<N>(u, m, t, 0, lane - t);                   // P(N-kx)
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int q = t + G * e;
+        if (q != 0) u[e] = cfma_(u[e], sw2[(SGN * q) & MASK], m[e]);   // V'(q); V'(0) = P(N)
+      }
+      group_fft<N, INV2>(u, scratch, tw, t);                   // even samples 2n of the column
+      if (act) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int n = t + G * e;
+          if (e < H) ybuf[tile(ky, 2 * n)] = u[e];
+          else ybuf[tile(ky, 2 * N - 1 - 2 * n)] = mk<V>(-u[e].x, -u[e].y);
+        }
+      }
+    }
+    __syncthreads();
+
+    // the next plane's first rows, read while this plane finishes
+    if constexpr (PREFETCH) {
+      if (next) load_row(next, line, v);
+    }
+
+    // pass 3: rows i, back along y
+#pragma unroll 1
+    for (int r0 = 0; r0 < N; r0 += GPC) {
+      const int il = r0 + line;
+      const int i = il < N ? il : 0;
+      V u[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int q = t + G * e;
+        if (q == 0) {
+          u[e] = ybuf[tile(N, i)];                             // V'(0) = P(N)
+        } else {
+          const V p = ybuf[tile(q, i)];
+          const V pm = ybuf[tile(N - q, i)];
+          u[e] = cfma_(p, sw2[(SGN * q) & MASK], pm);
+        }
+      }
+      group_fft<N, INV2>(u, scratch, tw, t);
+      if (il < N) {
+        V* out = pl + size_t(i) * N;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int n = t + G * e;
+          if (e < H) out[2 * n] = u[e];
+          else out[2 * N - 1 - 2 * n] = mk<V>(-u[e].x, -u[e].y);
+        }
+      }
+    }
+    if constexpr (!PREFETCH) {
+      if (next) load_row(next, line, v);
+    }
+  }
+};
+
+// one plane (used by the persistent batched kernel)
+template <typename T, int N, int THREADS, bool ADJ>
+__device__ __forceinline__ void tdst_plane(const SolveArgs<T>& a, int kz, unsigned char* smem_raw) {
+  using R = TDst<T, N, THREADS, ADJ>;
+  R r(a, smem_raw);
+  typename R::V v[R::E];
+  r.load_row(a.work + size_t(kz) * N * N, r.line, v);
+  r.load_tables(a);
+  __syncthreads();
+  r.plane(a, kz, v, nullptr);
+}
+
+// planes kz0, kz0 + stride, ... (the standalone kernel: one CTA per SM)
+template <typename T, int N, int THREADS, bool ADJ>
+__device__ __forceinline__ void tdst_planes(const SolveArgs<T>& a, int kz0, int stride,
+                                            unsigned char* smem_raw) {
+  using R = TDst<T, N, THREADS, ADJ>;
+  const int planes = a.nz + 1;
+  if (kz0 >= planes) return;
+  R r(a, smem_raw);
+  typename R::V v[R::E];
+  r.load_row(a.work + size_t(kz0) * N * N, r.line, v);
+  r.load_tables(a);
+  __syncthreads();
+#pragma unroll 1
+  for (int kz = kz0; kz < planes; kz += stride) {
+    const int nk = kz + stride;
+    r.plane(a, kz, v, nk < planes ? a.work + size_t(nk) * N * N : nullptr);
+    __syncthreads();
+  }
+}
+
+}  // namespace pp

@@ -1,5 +1,6 @@
 // Pipe-operator transverse stage: kernel and host launcher.  The device
 // routine and the description of the method are in tsym_impl.cuh.
+#include "tdst_impl.cuh"
 #include "tsym_impl.cuh"
 
 namespace pp {
@@ -64,6 +65,56 @@ static cudaError_t tclaunch(const SolveArgs<T>& a, cudaStream_t st) {
   }
 }
 
+// the N-point routine for cell-centred meshes.  Up to 256 threads: persistent
+// CTAs (as many as fit on the device at once) walking the kz planes, each
+// reading the next plane's first rows while it finishes the current one;
+// 512 threads (no registers to spare): one CTA per plane.
+template <typename T, int N, int THREADS, bool ADJ>
+__global__ void __launch_bounds__(THREADS, 1) transverse_dst_kernel(SolveArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if constexpr (TDst<T, N, THREADS, ADJ>::PREFETCH) tdst_planes<T, N, THREADS, ADJ>(a, blockIdx.x, gridDim.x, smem_raw);
+  else tdst_plane<T, N, THREADS, ADJ>(a, blockIdx.x, smem_raw);
+}
+
+template <typename T, int N, int THREADS, bool ADJ>
+static cudaError_t tdlaunch(const SolveArgs<T>& a, cudaStream_t st) {
+  using Cfg = TDstCfg<T, N, THREADS>;
+  if constexpr (Cfg::smem_bytes() > kMaxSmem) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    const size_t smem = Cfg::smem_bytes();
+    void (*kern)(SolveArgs<T>) = transverse_dst_kernel<T, N, THREADS, ADJ>;
+    static int resident = 0;                   // CTAs resident on the device at once
+    if (resident == 0) {
+      if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+      }
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      resident = sms * per_sm;
+    }
+    const int grid = (!TDst<T, N, THREADS, ADJ>::PREFETCH || a.nz + 1 < resident) ? a.nz + 1 : resident;
+    kern<<<grid, THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+}
+
+template <typename T, int N>
+static cudaError_t tdlaunch2(bool adjoint, int hb, int threads, const SolveArgs<T>& a, cudaStream_t st) {
+  if (hb != 1 || a.sx != 1 || a.sy != 1) return cudaErrorInvalidValue;
+  switch (threads) {
+    case 128: return adjoint ? tdlaunch<T, N, 128, true>(a, st) : tdlaunch<T, N, 128, false>(a, st);
+    case 256: return adjoint ? tdlaunch<T, N, 256, true>(a, st) : tdlaunch<T, N, 256, false>(a, st);
+    case 512: return adjoint ? tdlaunch<T, N, 512, true>(a, st) : tdlaunch<T, N, 512, false>(a, st);
+    default: return cudaErrorInvalidConfiguration;
+  }
+}
+
 template <typename T, int N>
 static cudaError_t tslaunch2(bool adjoint, int hb, int threads, const SolveArgs<T>& a, cudaStream_t st) {
   if (hb == 1 && threads == 512)            // cyclic-layout variant, 16 warps
@@ -87,10 +138,19 @@ static cudaError_t tslaunch2(bool adjoint, int hb, int threads, const SolveArgs<
 #endif
 
 template <>
-cudaError_t launch_transverse_sym<PP_TS_TYPE>(bool adjoint, int hb, int threads,
+cudaError_t launch_transverse_sym<PP_TS_TYPE>(bool adjoint, int kind, int hb, int threads,
                                               const SolveArgs<PP_TS_TYPE>& a, cudaStream_t st) {
   using T = PP_TS_TYPE;
   if (a.nx != a.ny || !a.images) return cudaErrorInvalidValue;
+  if (kind == 1) {
+    switch (a.nx) {
+      case 16: return tdlaunch2<T, 16>(adjoint, hb, threads, a, st);
+      case 32: return tdlaunch2<T, 32>(adjoint, hb, threads, a, st);
+      case 64: return tdlaunch2<T, 64>(adjoint, hb, threads, a, st);
+      case 128: return tdlaunch2<T, 128>(adjoint, hb, threads, a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (a.nx) {
     case 16: return tslaunch2<T, 16>(adjoint, hb, threads, a, st);
     case 32: return tslaunch2<T, 32>(adjoint, hb, threads, a, st);

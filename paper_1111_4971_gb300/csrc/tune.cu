@@ -5,7 +5,7 @@
 // autotuner times every variant that fits the device with CUDA events on the
 // caller's stream and keeps the fastest; results are cached per shape for the
 // process and, if PIPE_TUNE_CACHE names a file, persisted there as lines
-// "n nz dtype z_warps t_h t_threads".
+// "n nz dtype z_warps z_pipe t_h t_threads t_kind".
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -20,16 +20,26 @@
 
 namespace pp {
 
-Plan default_plan(int n, int nz, bool f64) {
+Plan default_plan(int n, int nz, bool f64, bool cell_centred) {
   Plan p;
-  p.z_warps = (!f64 && nz >= 512) ? 16 : 8;
-  // autotuned on GB300 at 128^2 x 1024: FP32 one 512-thread CTA per plane
-  // (cyclic-layout FFTs); FP64 2-CTA clusters of 128 threads
+  // timed on GB300: FP32 one CTA per plane, on cell-centred meshes with the
+  // n-point routine (256 threads; 512 at n = 64), else the cyclic 2n-point
+  // routine (512 threads); FP64 2-CTA clusters of 128 threads at n = 128
   p.z_warps = 8;
   p.z_pipe = 0;
-  if (!f64) { p.t_h = 1; p.t_threads = 512; }
-  else if (n < 128) { p.t_h = 1; p.t_threads = 256; }
-  else { p.t_h = 2; p.t_threads = 128; }
+  p.t_kind = 0;
+  if (!f64) {
+    p.t_h = 1;
+    if (cell_centred) { p.t_kind = 1; p.t_threads = n == 64 ? 512 : 256; }
+    else p.t_threads = 512;
+  } else if (n < 128) {
+    p.t_h = 1;
+    p.t_threads = 256;
+    if (cell_centred) p.t_kind = 1;
+  } else {
+    p.t_h = 2;
+    p.t_threads = 128;
+  }
   return p;
 }
 
@@ -59,10 +69,10 @@ void load_file_cache() {
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  int n, nz, dt, zw, th, tt;
+  int n, nz, dt, zw, th, tt, tk;
   int zp;
-  while (std::fscanf(f, "%d %d %d %d %d %d %d", &n, &nz, &dt, &zw, &zp, &th, &tt) == 7)
-    cache()[Key(n, nz, dt)] = Plan{zw, zp, th, tt};
+  while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &n, &nz, &dt, &zw, &zp, &th, &tt, &tk) == 8)
+    cache()[Key(n, nz, dt)] = Plan{zw, zp, th, tt, tk};
   std::fclose(f);
 }
 
@@ -71,8 +81,8 @@ void save_file_cache(const Key& k, const Plan& p) {
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), p.z_warps,
-               p.z_pipe, p.t_h, p.t_threads);
+  std::fprintf(f, "%d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), p.z_warps,
+               p.z_pipe, p.t_h, p.t_threads, p.t_kind);
   std::fclose(f);
 }
 
@@ -143,10 +153,14 @@ int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
       if (ms > 0 && ms < bz) { bz = ms; best.z_warps = zw; best.z_pipe = zp; }
     }
   if (h->images) {
-    const int shapes[7][2] = {{1, 128}, {1, 256}, {1, 512}, {2, 128}, {2, 256}, {4, 128}, {4, 256}};
+    // {kind, CTAs per plane, threads}; kind 1 only for cell-centred meshes
+    const int shapes[10][3] = {{0, 1, 128}, {0, 1, 256}, {0, 1, 512}, {0, 2, 128}, {0, 2, 256},
+                               {0, 4, 128}, {0, 4, 256}, {1, 1, 128}, {1, 1, 256}, {1, 1, 512}};
     for (auto& sh : shapes) {
-      float ms = time_ms([&] { return launch_transverse_sym<T>(false, sh[0], sh[1], a, st); }, st, reps);
-      if (ms > 0 && ms < bt) { bt = ms; best.t_h = sh[0]; best.t_threads = sh[1]; }
+      if (sh[0] == 1 && !(h->sx == 1 && h->sy == 1)) continue;
+      float ms = time_ms([&] { return launch_transverse_sym<T>(false, sh[0], sh[1], sh[2], a, st); }, st,
+                         reps);
+      if (ms > 0 && ms < bt) { bt = ms; best.t_kind = sh[0]; best.t_h = sh[1]; best.t_threads = sh[2]; }
     }
   } else {
     const int shapes[4][2] = {{1, 256}, {1, 512}, {2, 256}, {2, 512}};
@@ -197,26 +211,35 @@ extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
   return PIPE_OK;
 }
 
-extern "C" int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h, int* t_threads) {
-  if (!h || !z_warps || !z_pipe || !t_h || !t_threads) return PIPE_EINVAL;
+extern "C" int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h, int* t_threads,
+                             int* t_kind) {
+  if (!h || !z_warps || !z_pipe || !t_h || !t_threads || !t_kind) return PIPE_EINVAL;
   const Plan& p = h->images ? h->plan : h->free_plan;
   *z_warps = h->plan.z_warps;
   *z_pipe = h->plan.z_pipe;
   *t_h = p.t_h;
   *t_threads = p.t_threads;
+  *t_kind = p.t_kind;
   return PIPE_OK;
 }
 
-extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads) {
+extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads, int t_kind) {
   if (!h) return PIPE_EINVAL;
   if ((z_warps != 8 && z_warps != 16) || (z_pipe != 0 && z_pipe != 1) || (t_h != 1 && t_h != 2 && t_h != 4) ||
-      (t_threads != 128 && t_threads != 256 && t_threads != 512))
+      (t_threads != 128 && t_threads != 256 && t_threads != 512) || (t_kind != 0 && t_kind != 1))
     return PIPE_EINVAL;
-  if (h->images) h->plan = Plan{z_warps, z_pipe, t_h, t_threads};
+  if (t_kind == 1) {
+    // the N-point routine: pipe operator on cell-centred meshes, one CTA per
+    // plane, the N x N plane buffer in shared memory
+    if (!h->images || h->sx != 1 || h->sy != 1 || t_h != 1) return PIPE_EUNSUPPORTED;
+    const size_t c = h->grid.dtype == PIPE_F64 ? 16 : 8;
+    if (c * h->grid.nx * h->grid.ny > 200 * 1024) return PIPE_EUNSUPPORTED;
+  }
+  if (h->images) h->plan = Plan{z_warps, z_pipe, t_h, t_threads, t_kind};
   else {
     h->plan.z_warps = z_warps;
     h->plan.z_pipe = z_pipe;
-    h->free_plan = Plan{z_warps, z_pipe, t_h, t_threads};
+    h->free_plan = Plan{z_warps, z_pipe, t_h, t_threads, 0};
   }
   return PIPE_OK;
 }

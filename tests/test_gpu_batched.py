@@ -25,7 +25,9 @@ def make_set(count, seed=4, dtype=torch.float32):
     solvers, rhos = [], []
     for it in items:
         s = PipeSolver(it["geom"], it["grid"], igf=True, dtype=dtype)
-        s.set_plan(z_warps=16, z_pipe=0, t_h=1, t_threads=512)   # the transverse shape of the batched kernel
+        # the shapes of the persistent kernel: 16-warp z tiles, one 512-thread
+        # CTA per plane with the n-point routine (cell-centred meshes)
+        s.set_plan(z_warps=16, z_pipe=0, t_h=1, t_threads=512, t_kind=1)
         solvers.append(s)
         rhos.append(torch.tensor(it["rho"], dtype=dtype, device="cuda"))
     return items, solvers, rhos

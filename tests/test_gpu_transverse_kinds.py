@@ -1,0 +1,99 @@
+"""The n-point transverse routine (plan t_kind = 1, cell-centred meshes)
+against the same references as the default routine: the padded four-term
+transverse stage per kz plane, and full solves against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from inputs.bunches import Geometry, Grid, cell_centred, random_density
+from oracle import pipe
+from test_gpu_parity import F32_TOL, F64_TOL, GEOMS, _transverse_reference, dev, host, rel, solver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1111_4971_gb300 import build
+    build.build()
+
+
+CELL = {
+    "cc16x16x32": GEOMS["cc16x16x32"],
+    "rect32x32x64": GEOMS["rect32x32x64"],
+    "aliased32x32x32": GEOMS["aliased32x32x32"],
+    "rect64x64x32": cell_centred(3.0, 1.0, 64, 64, 32, 0.05, modes=20),
+    "sq128x128x32": cell_centred(1.0, 1.0, 128, 128, 32, 0.02, modes=20),
+}
+
+
+def _plan(s, threads):
+    p = s.plan
+    s.set_plan(z_warps=p["z_warps"], z_pipe=p["z_pipe"], t_h=1, t_threads=threads, t_kind=1)
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512])
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 5e-6)])
+@pytest.mark.parametrize("key", list(CELL))
+def test_stage_transverse_npoint(key, dtype, tol, threads):
+    geom, grid = CELL[key]
+    if dtype == torch.float64 and grid.nx > 64:
+        pytest.skip("the FP64 n-point routine holds planes up to 64^2")
+    s = solver(geom, grid, 1, dtype)
+    _plan(s, threads)
+    rng = np.random.default_rng(grid.nx + threads)
+    P = rng.standard_normal((grid.nz + 1, grid.nx, grid.ny)) \
+        + 1j * rng.standard_normal((grid.nz + 1, grid.nx, grid.ny))
+    cdt = torch.complex128 if dtype == torch.float64 else torch.complex64
+    for adj in (0, 1):
+        spec = torch.tensor(P, dtype=cdt, device="cuda")
+        s.stage_transverse(spec, adjoint=adj)
+        want = _transverse_reference(P, geom, grid, 1, adj)
+        assert rel(spec.cpu().numpy(), want) < tol, (adj, rel(spec.cpu().numpy(), want))
+
+
+@pytest.mark.parametrize("igf", [0, 1])
+@pytest.mark.parametrize("key", ["rect32x32x64", "rect64x64x32", "sq128x128x32"])
+def test_solve_and_adjoint_npoint_against_oracle(key, igf):
+    geom, grid = CELL[key]
+    rho = random_density(grid.shape, 200 + igf, sparsity=0.3)
+    spectra = pipe.green_spectra(geom, grid, igf)
+    want = pipe.fft_solve(rho, geom, grid, igf, spectra=spectra)
+    want_adj = pipe.fft_adjoint(rho, geom, grid, igf, spectra=spectra)
+    for dtype, tol in ((torch.float64, F64_TOL), (torch.float32, F32_TOL)):
+        if dtype == torch.float64 and grid.nx > 64:
+            continue
+        s = solver(geom, grid, igf, dtype)
+        _plan(s, 512 if grid.nx >= 64 else 256)
+        assert s.plan["t_kind"] == 1
+        assert rel(host(s.solve(dev(rho, dtype))), want) <= tol
+        assert rel(host(s.adjoint(dev(rho, dtype))), want_adj) <= tol
+
+
+def test_npoint_matches_padded_routine_on_the_bench_grid():
+    """128^2 x 1024 FP32: the two routines agree to rounding on the long bunch."""
+    from inputs import bunches
+    w = bunches.workload_throughput_128()
+    geom, grid, rho = w["geom"], w["grid"], w["rho"][0]
+    s = solver(geom, grid, 1, torch.float32)
+    s.set_plan(z_warps=8, z_pipe=0, t_h=1, t_threads=512, t_kind=0)
+    a = host(s.solve(dev(rho, torch.float32)))
+    _plan(s, 512)
+    b = host(s.solve(dev(rho, torch.float32)))
+    assert rel(b, a) <= 2e-6
+
+
+def test_npoint_plan_refused_where_it_does_not_apply():
+    from paper_1111_4971_gb300 import PipeError
+    geom, grid = GEOMS["wall16x16x64"]                  # x0 = 0: s = 0
+    s = solver(geom, grid, 1, torch.float64)
+    with pytest.raises(PipeError):
+        s.set_plan(z_warps=8, z_pipe=0, t_h=1, t_threads=256, t_kind=1)
+    geom, grid = CELL["sq128x128x32"]                   # FP64 plane of 256 KB
+    s = solver(geom, grid, 1, torch.float64)
+    with pytest.raises(PipeError):
+        s.set_plan(z_warps=8, z_pipe=0, t_h=1, t_threads=512, t_kind=1)
+    with pytest.raises(PipeError):                      # one CTA per plane only
+        s.set_plan(z_warps=8, z_pipe=0, t_h=2, t_threads=256, t_kind=1)
