@@ -35,12 +35,12 @@ WORKLOAD = "pipe128x128x1024_igf"
 # recorded DRAM traffic is reported only while these files hash to the value
 # written next to it (a changed kernel reports traffic null)
 KERNEL_SOURCES = {
-    "transverse": ["tsym_impl.cuh", "transverse_sym.cu", "fft_common.cuh", "solver.cuh"],
+    "transverse": ["tdst_impl.cuh", "transverse_sym.cu", "fft_common.cuh", "solver.cuh"],
     "z_forward": ["zfft_impl.cuh", "zfft.cu", "fft_common.cuh", "solver.cuh"],
     "z_inverse": ["zfft_impl.cuh", "zfft.cu", "fft_common.cuh", "solver.cuh"],
 }
 PROFILE_FILES = {
-    "transverse": "transverse_cyc_pipe128x128x1024_igf_f32.md",
+    "transverse": "transverse_dst_pipe128x128x1024_igf_f32.md",
     "z_forward": "zfft_pipe128x128x1024_igf_f32.md",
     "z_inverse": "zfft_pipe128x128x1024_igf_f32.md",
 }

@@ -66,9 +66,6 @@ struct TDst {
   static constexpr bool INV1 = ADJ, INV2 = !ADJ;
   static constexpr int MASK = 2 * N - 1;
   static constexpr int SGN = ADJ ? 1 : -1;                     // w^{-q} = sw2[(SGN q) mod 2N]
-  // with registers to spare (at most 256 threads), the next rows' loads are
-  // issued before the current rows are transformed
-  static constexpr bool PREFETCH = THREADS <= 256;
 
   V* ybuf;
   V* sw2;                                                      // 2N phases w_{2N}^j
@@ -110,23 +107,18 @@ struct TDst {
     for (int i = threadIdx.x; i < 2 * N; i += THREADS) sw2[i] = a.w2_t[i];
   }
 
-  // Plane kz in place.  On entry v holds this plane's row `line` (load_row);
-  // on return, if next != nullptr, it holds row `line` of the plane at next.
+  // Plane kz in place (the phase table already loaded and synchronised).
   // Ends with the plane's stores issued; the caller synchronises before
   // another plane reuses the buffers.
-  __device__ __forceinline__ void plane(const SolveArgs<T>& a, int kz, V (&v)[E], const V* next) {
+  __device__ __forceinline__ void plane(const SolveArgs<T>& a, int kz) {
     V* pl = a.work + size_t(kz) * N * N;
 
     // pass 1: rows i, along y -> ybuf[ky][i], ky = 1..N
 #pragma unroll 1
     for (int r0 = 0; r0 < N; r0 += GPC) {
       const int il = r0 + line;
-      V nxt[PREFETCH ? E : 1];
-      if constexpr (PREFETCH) {
-        if (r0 + GPC < N) load_row(pl, r0 + GPC + line, nxt);
-      } else {
-        if (r0 > 0) load_row(pl, il, v);
-      }
+      V v[E];
+      load_row(pl, il, v);
       group_fft<N, INV1>(v, scratch, tw, t);                   // V(q)
       V m[E];
       mirror_fetch<N>(v, m, t, 0, lane - t);                   // V(N-q)
@@ -136,12 +128,6 @@ struct TDst {
           const int q = t + G * e;
           if (q == 0) ybuf[tile(N, il)] = mk<V>(v[e].x + v[e].x, v[e].y + v[e].y);
           else ybuf[tile(q, il)] = cfms(v[e], sw2[(SGN * q) & MASK], m[e]);
-        }
-      }
-      if constexpr (PREFETCH) {
-        if (r0 + GPC < N) {
-#pragma unroll
-          for (int e = 0; e < E; ++e) v[e] = nxt[e];
         }
       }
     }
@@ -164,27 +150,18 @@ struct TDst {
           u[e] = mk<V>(-x.x, -x.y);
         }
       }
-      const T* grow = a.green + (size_t(kz) * (N + 1) + ky) * (N + 1);
-      T g[E];                                   // Green row: before the transform if registers allow
-      auto load_g = [&] {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int kx = t + G * e;
-          g[e] = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
-        }
-      };
-      if constexpr (PREFETCH) load_g();
       group_fft<N, INV1>(u, scratch, tw, t);                   // V(kx)
-      if constexpr (!PREFETCH) load_g();
       V m[E];
       mirror_fetch<N>(u, m, t, 0, lane - t);
+      const T* grow = a.green + (size_t(kz) * (N + 1) + ky) * (N + 1);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int kx = t + G * e;
+        const T g = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
         // slot 0 carries kx = N: U(N) = 2 V(0)
         const V w = (kx == 0) ? mk<V>(u[e].x + u[e].x, u[e].y + u[e].y)
                               : cfms(u[e], sw2[(SGN * kx) & MASK], m[e]);
-        u[e] = cscale(w, g[e]);                                // P(kx)
+        u[e] = cscale(w, g);                                   // P(kx)
       }
       mirror_fetch<N>(u, m, t, 0, lane - t);                   // P(N-kx)
 #pragma unroll
@@ -203,11 +180,6 @@ struct TDst {
       }
     }
     __syncthreads();
-
-    // the next plane's first rows, read while this plane finishes
-    if constexpr (PREFETCH) {
-      if (next) load_row(next, line, v);
-    }
 
     // pass 3: rows i, back along y
 #pragma unroll 1
@@ -237,42 +209,16 @@ struct TDst {
         }
       }
     }
-    if constexpr (!PREFETCH) {
-      if (next) load_row(next, line, v);
-    }
   }
 };
 
-// one plane (used by the persistent batched kernel)
+// one plane
 template <typename T, int N, int THREADS, bool ADJ>
 __device__ __forceinline__ void tdst_plane(const SolveArgs<T>& a, int kz, unsigned char* smem_raw) {
-  using R = TDst<T, N, THREADS, ADJ>;
-  R r(a, smem_raw);
-  typename R::V v[R::E];
-  r.load_row(a.work + size_t(kz) * N * N, r.line, v);
+  TDst<T, N, THREADS, ADJ> r(a, smem_raw);
   r.load_tables(a);
   __syncthreads();
-  r.plane(a, kz, v, nullptr);
-}
-
-// planes kz0, kz0 + stride, ... (the standalone kernel: one CTA per SM)
-template <typename T, int N, int THREADS, bool ADJ>
-__device__ __forceinline__ void tdst_planes(const SolveArgs<T>& a, int kz0, int stride,
-                                            unsigned char* smem_raw) {
-  using R = TDst<T, N, THREADS, ADJ>;
-  const int planes = a.nz + 1;
-  if (kz0 >= planes) return;
-  R r(a, smem_raw);
-  typename R::V v[R::E];
-  r.load_row(a.work + size_t(kz0) * N * N, r.line, v);
-  r.load_tables(a);
-  __syncthreads();
-#pragma unroll 1
-  for (int kz = kz0; kz < planes; kz += stride) {
-    const int nk = kz + stride;
-    r.plane(a, kz, v, nk < planes ? a.work + size_t(nk) * N * N : nullptr);
-    __syncthreads();
-  }
+  r.plane(a, kz);
 }
 
 }  // namespace pp

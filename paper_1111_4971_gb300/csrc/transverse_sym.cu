@@ -65,15 +65,11 @@ static cudaError_t tclaunch(const SolveArgs<T>& a, cudaStream_t st) {
   }
 }
 
-// the N-point routine for cell-centred meshes.  Up to 256 threads: persistent
-// CTAs (as many as fit on the device at once) walking the kz planes, each
-// reading the next plane's first rows while it finishes the current one;
-// 512 threads (no registers to spare): one CTA per plane.
+// the N-point routine for cell-centred meshes: one CTA per kz plane
 template <typename T, int N, int THREADS, bool ADJ>
 __global__ void __launch_bounds__(THREADS, 1) transverse_dst_kernel(SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if constexpr (TDst<T, N, THREADS, ADJ>::PREFETCH) tdst_planes<T, N, THREADS, ADJ>(a, blockIdx.x, gridDim.x, smem_raw);
-  else tdst_plane<T, N, THREADS, ADJ>(a, blockIdx.x, smem_raw);
+  tdst_plane<T, N, THREADS, ADJ>(a, blockIdx.x, smem_raw);
 }
 
 template <typename T, int N, int THREADS, bool ADJ>
@@ -84,22 +80,11 @@ static cudaError_t tdlaunch(const SolveArgs<T>& a, cudaStream_t st) {
   } else {
     const size_t smem = Cfg::smem_bytes();
     void (*kern)(SolveArgs<T>) = transverse_dst_kernel<T, N, THREADS, ADJ>;
-    static int resident = 0;                   // CTAs resident on the device at once
-    if (resident == 0) {
-      if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-      }
-      int dev = 0, sms = 0, per_sm = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
-      if (per_sm < 1) return cudaErrorInvalidConfiguration;
-      resident = sms * per_sm;
     }
-    const int grid = (!TDst<T, N, THREADS, ADJ>::PREFETCH || a.nz + 1 < resident) ? a.nz + 1 : resident;
-    kern<<<grid, THREADS, smem, st>>>(a);
+    kern<<<a.nz + 1, THREADS, smem, st>>>(a);
     return cudaGetLastError();
   }
 }
