@@ -201,3 +201,16 @@ def windowed(geom: Geometry, grid: Grid, a: float, b: float, modes: int | None =
     y0 = 0.5 * (b - (grid.ny - 1) * grid.hy)
     m = geom.modes_m if modes is None else modes
     return replace(geom, a=a, b=b, x0=x0, y0=y0, modes_m=m, modes_n=m)
+
+
+def accuracy_study_case(sigma_z: float, n: int, nz: int, modes: int = 20):
+    """Accuracy-study bunch (Sec. 4, Figs. 2-4): square pipe a = b = 1, wall-node
+    mesh (x0 = y0 = 0, n*h = a, so node n/2 lies on the axis), Gaussian with
+    sigma_x = sigma_y = 0.15 a and the given sigma_z, centred on the axis at
+    z = Lz/2 with Lz = 8 sigma_z; nodes z_k = k*Lz/nz, so a coarse node k is the
+    fine node k*(nz_fine/nz).  Unit total charge."""
+    geom = Geometry(1.0, 1.0, 0.0, 0.0, modes, modes)
+    lz = 8.0 * sigma_z
+    grid = Grid(n, n, nz, 1.0 / n, 1.0 / n, lz / nz)
+    rho = gaussian_bunch(geom, grid, (0.5, 0.5, 0.5 * lz), (0.15, 0.15, sigma_z))
+    return geom, grid, rho

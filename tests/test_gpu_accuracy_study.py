@@ -1,0 +1,73 @@
+"""Accuracy study of Sec. 4 (Figs. 2-4): on-axis potential with the ordinary
+(Eq. 9) and the integrated (Eq. 16) Green function on coarse grids, against a
+fine IGF solve, for bunches shorter than, a few times longer than, and much
+longer than the pipe width (sigma_z = 0.3 a, 3 a, 30 a; sigma_x = sigma_y =
+0.15 a, as 1.2 cm / 12 cm / 1.2 m bunches of 6 mm width in a 4 cm pipe).
+
+The paper's reference is an IGF solve on 512^2 x 1024; the finest grid this
+library supports is 128^2 x 1024, which serves as the reference here.  The
+assertions are the paper's qualitative statements: for the short bunch both
+Green functions are within 1 %; for the longer ones the ordinary Green function
+is off by percents to tens of percents (sigma_z = 3 a) or by more than 100 %
+(sigma_z = 30 a) on coarse grids, while the IGF stays within 1 %."""
+import numpy as np
+import pytest
+import torch
+
+from inputs.bunches import accuracy_study_case
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = [(64, 128), (64, 256), (128, 256), (128, 512)]
+REF = (128, 1024)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1111_4971_gb300 import build
+    build.build()
+
+
+def on_axis(sigma_z, n, nz, igf):
+    from paper_1111_4971_gb300 import PipeSolver
+    geom, grid, rho = accuracy_study_case(sigma_z, n, nz)
+    s = PipeSolver(geom, grid, igf=igf, dtype=torch.float64)
+    phi = s.solve(torch.tensor(rho, device="cuda"))
+    torch.cuda.synchronize()
+    return np.arange(nz) * grid.hz, phi[n // 2, n // 2, :].cpu().numpy()
+
+
+def study(sigma_z):
+    """max pointwise relative error on the axis within 2 sigma_z of the centre"""
+    _, ref = on_axis(sigma_z, *REF, 1)
+    out = {}
+    for n, nz in GRIDS:
+        for igf in (0, 1):
+            z, p = on_axis(sigma_z, n, nz, igf)
+            r = ref[:: REF[1] // nz]
+            core = np.abs(z - 4.0 * sigma_z) <= 2.0 * sigma_z
+            out[(n, nz, igf)] = float(np.max(np.abs(p[core] - r[core]) / np.abs(r[core])))
+    for (n, nz, igf), e in out.items():
+        print(f"sigma_z={sigma_z:5.1f} a  {n}^2x{nz}  {'IGF     ' if igf else 'ordinary'}  {e:.2e}")
+    return out
+
+
+def test_short_bunch_both_green_functions_accurate():
+    err = study(0.3)
+    assert all(e < 0.01 for e in err.values())
+
+
+def test_bunch_three_pipe_widths_ordinary_green_function_degrades():
+    err = study(3.0)
+    assert all(err[(n, nz, 1)] < 0.01 for n, nz in GRIDS)
+    assert err[(64, 128, 0)] > 0.05 and err[(64, 256, 0)] > 0.02
+    # the ordinary result converges as the z mesh resolves exp(-kappa |w|)
+    assert err[(128, 256, 0)] > err[(128, 512, 0)]
+
+
+def test_very_long_bunch_ordinary_error_exceeds_100_percent():
+    err = study(30.0)
+    assert all(err[(n, nz, 1)] < 0.01 for n, nz in GRIDS)
+    assert err[(64, 128, 0)] > 1.0 and err[(64, 256, 0)] > 1.0
