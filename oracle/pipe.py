@@ -16,6 +16,10 @@ O2  ``naive_dft_solve``   Eq. 10 literally: zero-padded rho, one forward
                           matrices applied per axis.
 O3  ``fft_solve``         the same with scipy.fft.
 
+The banded reduction of Sec. 5 (Eq. 17-18: only source planes within n_nb of
+the output plane) has its own pair: ``direct_sum_banded`` (O1 restricted to
+the band) and ``banded_solve`` (2-D transforms per z-offset).
+
 Conventions (Sec. 1 below Eq. 5, Eq. A.4): the forward transform f is
 sum_n a_n e^{-2 pi i nk/N}, the backward transform b is sum_n a_n e^{+2 pi i nk/N};
 a *final* transform carries 1/N per dimension (Eq. A.4), whatever its
@@ -63,6 +67,41 @@ def mesh(geom, grid):
 # ---------------------------------------------------------------------------
 # O1: brute-force sum (Eq. 4 with Eq. 7)
 # ---------------------------------------------------------------------------
+
+def direct_sum_banded(rho, geom, grid, igf, n_nb):
+    """Eq. 18 by brute force: the sum of O1 with the source planes restricted
+    to |k - k'| <= n_nb (n_nb = 0 is Eq. 17, one 2-D sum per plane)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    G4 = _pair_green(geom, grid, igf)
+    nz = grid.nz
+    phi = np.empty(rho.shape)
+    for k in range(nz):
+        kp = np.arange(max(0, k - n_nb), min(nz, k + n_nb + 1))
+        sl = G4[..., k - kp + nz - 1]
+        phi[:, :, k] = np.einsum("ikjlq,klq->ij", sl, rho[:, :, kp])
+    return h3(grid) * phi
+
+
+def banded_solve(rho, geom, grid, igf, n_nb, workers=None):
+    """Eq. 18 with transforms: for every output plane k, the sum over
+    d = -n_nb..n_nb of the 2-D mixed convolution/correlation (the x, y part of
+    Eq. 10, on the doubled transverse grid) of source plane k - d with the R
+    tables at z-offset d*hz.  Source planes outside 0..nz-1 are zero."""
+    nx, ny, nz = grid.shape
+    T = green_tables(geom, grid, igf)                  # z offsets d at slot d mod 2nz
+    P = np.zeros((2 * nx, 2 * ny, nz))
+    P[:nx, :ny, :] = rho
+    P_hat = transform(P, "ff", workers=workers)        # x and y only
+    acc = np.zeros(P_hat.shape, dtype=np.complex128)
+    for d in range(-n_nb, n_nb + 1):
+        S = np.zeros_like(P_hat)
+        lo, hi = max(0, d), min(nz, nz + d)            # planes k with 0 <= k - d < nz
+        S[:, :, lo:hi] = P_hat[:, :, lo - d:hi - d]
+        for sign, kx, ky, gdir, fdir in TERMS:
+            spec = transform(T[kx + ky][:, :, d % (2 * nz)], gdir[:2], workers=workers)
+            acc += sign * transform(S * spec[:, :, None], fdir[:2], final=True, workers=workers)
+    return h3(grid) * acc[:nx, :ny, :].real
+
 
 def _pair_green(geom, grid, igf):
     """G4[i, i', j, j', d] = G(x_i, x_i', y_j, y_j', (d - nz + 1) hz), Eq. 7.

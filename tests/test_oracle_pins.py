@@ -364,3 +364,48 @@ def test_energy_gradient_fd():
         fd = (wp - wm) / 2e-3
         assert abs(fd - grad[idx]) < 1e-9 * max(1.0, abs(fd))
         assert abs(grad[idx] - phi[idx]) < 1e-12 * max(1.0, abs(phi[idx]))
+
+
+# ---------------------------------------------------------------------------
+# Banded reduction (Sec. 5, Eq. 17-18): two independent evaluations agree, and
+# the band covering every plane is the full solve
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_nb", [0, 1, 3])
+@pytest.mark.parametrize("igf", [0, 1])
+@pytest.mark.parametrize("name,geom,grid", CASES, ids=[c[0] for c in CASES])
+def test_banded_solvers_agree(name, geom, grid, igf, n_nb):
+    rho = random_density(grid.shape, 13, sparsity=0.3)
+    p1 = pipe.direct_sum_banded(rho, geom, grid, igf, n_nb)
+    p2 = pipe.banded_solve(rho, geom, grid, igf, n_nb)
+    assert rel(p2, p1) < 1e-12
+
+
+@pytest.mark.parametrize("igf", [0, 1])
+def test_full_band_is_the_full_solve(igf):
+    geom, grid = cell_centred(2.0, 1.5, 4, 6, 8, 0.2, modes=7)
+    rho = random_density(grid.shape, 17)
+    full = pipe.fft_solve(rho, geom, grid, igf)
+    assert rel(pipe.banded_solve(rho, geom, grid, igf, grid.nz - 1), full) < 1e-12
+    assert rel(pipe.direct_sum_banded(rho, geom, grid, igf, grid.nz - 1), full) < 1e-12
+    # a narrower band drops the terms beyond it: the difference is exactly
+    # the contribution of the source planes outside the band
+    part = pipe.banded_solve(rho, geom, grid, igf, 2)
+    k = 5
+    near = np.zeros_like(rho)
+    near[:, :, k - 2:k + 3] = rho[:, :, k - 2:k + 3]
+    assert rel(part[:, :, k], pipe.fft_solve(near, geom, grid, igf)[:, :, k]) < 1e-12
+    assert rel(part, full) > 1e-6
+
+
+def test_banded_long_bunch_close_to_full():
+    """Sec. 5: for a bunch much longer than the pipe on a coarse z mesh
+    (hz = 15 a) the IGF falls off so fast that the 2-D reduction (Eq. 17)
+    is within a few percent of the full solve, and one neighbour on each side
+    (Eq. 18) leaves out only terms below e^{-kappa hz} ~ 1e-29."""
+    geom, grid, rho = bunches.accuracy_study_case(30.0, 8, 16, modes=6)
+    full = pipe.fft_solve(rho, geom, grid, 1)
+    e0 = rel(pipe.banded_solve(rho, geom, grid, 1, 0), full)
+    e1 = rel(pipe.banded_solve(rho, geom, grid, 1, 1), full)
+    assert 1e-3 < e0 < 0.03
+    assert e1 < 1e-13
