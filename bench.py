@@ -263,6 +263,49 @@ def bench_batched(args, count=96):
             "launches_per_batch": (1 if persistent else 0) + 3 * (count - persistent)}
 
 
+def bench_banded(args):
+    """Banded reduction (Sec. 5, Eq. 17-18) against the full solve on a bunch
+    30 pipe widths long, 128^2 x 1024 cell-centred, FP32: solves/s and the
+    relative difference to the full solve for a few band widths."""
+    import torch
+
+    from inputs.bunches import cell_centred, gaussian_bunch
+    from paper_1111_4971_gb300 import PipeSolver
+    geom, grid = cell_centred(1.0, 1.0, 128, 128, 1024, 240.0 / 1024, modes=20)
+    rho = torch.tensor(gaussian_bunch(geom, grid, (0.5, 0.5, 120.0), (0.15, 0.15, 30.0)),
+                       dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def timed(s, out, reps=10):
+        for _ in range(3):
+            s.solve(rho, out)
+        ts = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.solve(rho, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    full = PipeSolver(geom, grid, igf=True, dtype=torch.float32)
+    pf = full.empty()
+    t_full = timed(full, pf)
+    ref = pf.double()
+    out = {"workload": "pipe128x128x1024_igf_sigmaz30a", "full_ms": t_full, "bands": []}
+    for nb in (0, 2, 8, 16):
+        s = PipeSolver(geom, grid, igf=True, dtype=torch.float32, banded=nb)
+        p = s.empty()
+        t = timed(s, p)
+        err = float((p.double() - ref).norm() / ref.norm())
+        out["bands"].append({"n_neighbors": nb, "ms": t, "speedup_vs_full": t_full / t,
+                             "rel_l2_vs_full": err})
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -437,6 +480,7 @@ def run_ours(args):
 
     if rank == 0 and not args.quick:
         line["batched"] = bench_batched(args)
+        line["banded"] = bench_banded(args)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times, cores, _ = cpu_oracle_baseline(w, steps=1)

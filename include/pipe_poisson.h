@@ -91,6 +91,27 @@ typedef struct pipe_handle pipe_handle;
 int pipe_green_setup(const pipe_geometry* geometry, const pipe_grid* grid, int igf,
                      pipe_handle** out);
 
+/* The banded reduction of Sec. 5 (Eq. 17-18): a handle whose solve computes,
+ * for every z plane k, only the source planes k' with |k - k'| <= n_neighbors:
+ *     phi_ijk = hx hy hz sum_{|k-k'| <= n_neighbors} sum_{i'j'} rho_{i'j'k'} G(..., (k-k') hz)
+ * (n_neighbors = 0 is Eq. 17: one 2-D mixed convolution/correlation per
+ * plane).  Accurate when the Green function (usually the IGF on a z mesh
+ * coarse against the pipe width) is negligible beyond n_neighbors planes;
+ * n_neighbors = nz - 1 reproduces the full solve.  No transform along z is
+ * taken: the 2-D spectra of the tables at offsets 0..n_neighbors are computed
+ * once (FP64) and the solve is two kernels over pairs of z planes.
+ * pipe_poisson_solve and pipe_poisson_adjoint (the same operator: it is
+ * symmetric) and pipe_poisson_solve_host accept the handle; the stage,
+ * no-alloc and batched entry points return PIPE_EUNSUPPORTED for it.
+ * Requirements beyond pipe_green_setup's: cell-centred mesh (2*x0/hx ==
+ * 2*y0/hy == 1) and an nx*ny complex plane of at most 200 KB (FP32 up to
+ * 128^2, FP64 up to 64^2).  pipe_green_spectrum returns its
+ * (nx+1)*(ny+1)*(n_neighbors+1) planes [d][ky][kx], scaled by
+ * hx*hy*hz/(4*nx*ny).  Errors: as pipe_green_setup, plus PIPE_EINVAL for
+ * n_neighbors < 0 or >= nz. */
+int pipe_banded_setup(const pipe_geometry* geometry, const pipe_grid* grid, int igf, int n_neighbors,
+                      pipe_handle** out);
+
 /* Free-space (Hockney) comparison handle: Eq. 5 with G = 1/r (Eq. 3) tabulated
  * on the doubled grid with convolution offsets in x, y and z.  The paper does
  * not give G(0,0,0); `self_value` supplies it (<= 0 selects 1/min(hx,hy,hz)).

@@ -38,10 +38,14 @@ class PipeSolver:
     ``geometry``: object with a, b, x0, y0, modes_m, modes_n.
     ``grid``: object with nx, ny, nz, hx, hy, hz.
     ``dtype``: torch.float32 or torch.float64 (the solve's arithmetic type).
+    ``banded``: None for the full solve (Eq. 10); an int n >= 0 for the banded
+    reduction of Sec. 5 (Eq. 17-18) keeping source planes within n of each
+    output plane.
     """
 
     def __init__(self, geometry, grid, igf: bool = True, dtype=torch.float32, *,
-                 free_space: bool = False, self_value: float = 0.0, device=None):
+                 free_space: bool = False, self_value: float = 0.0, banded: int | None = None,
+                 device=None):
         self.lib = _lib.load()
         self.dtype = dtype
         self.shape = (int(grid.nx), int(grid.ny), int(grid.nz))
@@ -49,6 +53,7 @@ class PipeSolver:
         self.geometry = geometry
         self.igf = bool(igf)
         self.free_space = free_space
+        self.banded = banded
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         g = PipeGrid(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.hx), float(grid.hy),
                      float(grid.hz), _lib.PIPE_F64 if dtype == torch.float64 else _lib.PIPE_F32)
@@ -59,9 +64,14 @@ class PipeSolver:
             else:
                 geo = PipeGeometry(float(geometry.a), float(geometry.b), float(geometry.x0),
                                    float(geometry.y0), int(geometry.modes_m), int(geometry.modes_n))
-                st = self.lib.pipe_green_setup(ctypes.byref(geo), ctypes.byref(g), int(bool(igf)),
-                                               ctypes.byref(h))
-        check(st, "pipe_green_setup" if not free_space else "pipe_free_space_setup")
+                if banded is None:
+                    st = self.lib.pipe_green_setup(ctypes.byref(geo), ctypes.byref(g), int(bool(igf)),
+                                                   ctypes.byref(h))
+                else:
+                    st = self.lib.pipe_banded_setup(ctypes.byref(geo), ctypes.byref(g), int(bool(igf)),
+                                                    int(banded), ctypes.byref(h))
+        check(st, "pipe_free_space_setup" if free_space else
+              ("pipe_green_setup" if banded is None else "pipe_banded_setup"))
         self.handle = h
 
     # -- helpers ---------------------------------------------------------
@@ -104,7 +114,8 @@ class PipeSolver:
     def green_spectrum(self):
         import numpy as np
         nx, ny, nz = self.shape
-        out = np.empty((nz + 1, ny + 1, nx + 1), dtype=np.float64)
+        planes = nz + 1 if self.banded is None else self.banded + 1
+        out = np.empty((planes, ny + 1, nx + 1), dtype=np.float64)
         check(self.lib.pipe_green_spectrum(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                            out.size), "pipe_green_spectrum")
         return out

@@ -39,6 +39,7 @@ H = c_void_p  # pipe_handle*
 SIGNATURES = {
     "pipe_green_setup": (c_int, [POINTER(PipeGeometry), POINTER(PipeGrid), c_int, POINTER(H)]),
     "pipe_free_space_setup": (c_int, [POINTER(PipeGrid), c_double, POINTER(H)]),
+    "pipe_banded_setup": (c_int, [POINTER(PipeGeometry), POINTER(PipeGrid), c_int, c_int, POINTER(H)]),
     "pipe_poisson_solve": (c_int, [H, c_void_p, c_void_p, c_void_p]),
     "pipe_poisson_adjoint": (c_int, [H, c_void_p, c_void_p, c_void_p]),
     "pipe_poisson_solve_host": (c_int, [H, c_void_p, c_void_p, c_void_p]),

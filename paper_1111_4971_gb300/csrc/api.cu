@@ -71,7 +71,8 @@ size_t cplx_size(int dtype) { return dtype == PIPE_F64 ? 16 : 8; }
 // allocate everything but the Green spectrum; fill the twiddle tables
 int alloc_common(pipe_handle* h) {
   const pipe_grid& g = h->grid;
-  const size_t oct = size_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+  // Green planes: the 3-D octant, or the n_nb + 1 2-D spectra of the banded form
+  const size_t oct = size_t(g.nx + 1) * (g.ny + 1) * (h->banded >= 0 ? h->banded + 1 : g.nz + 1);
   const size_t work = size_t(g.nz + 1) * g.nx * g.ny * cplx_size(g.dtype);
   cudaError_t e;
   if ((e = cudaMalloc(&h->green64, oct * sizeof(double))) != cudaSuccess) return status_of(e);
@@ -152,6 +153,8 @@ template <typename T>
 int run_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStream_t st) {
   SolveArgs<T> a = make_args<T>(h, rho, phi, h->work);
   cudaError_t e;
+  // the banded operator is symmetric: the adjoint is the same computation
+  if (h->banded >= 0) return status_of(launch_banded<T>(h->plan.t_threads, a, h->banded, st));
   const int zw = h->plan.z_warps, zp = h->plan.z_pipe;
   if ((e = launch_z<T>(true, zw, zp, adjoint, a, st)) != cudaSuccess) return status_of(e);
   if ((e = transverse_stage<T>(h, adjoint, a, st)) != cudaSuccess) return status_of(e);
@@ -214,7 +217,8 @@ double pipe_selftest_twiddles(void) {
   return worst;
 }
 
-int pipe_green_setup(const pipe_geometry* geom, const pipe_grid* grid, int igf, pipe_handle** out) {
+static int setup_pipe(const pipe_geometry* geom, const pipe_grid* grid, int igf, int n_nb,
+                      pipe_handle** out) {
   if (!out) return PIPE_EINVAL;
   *out = nullptr;
   if (!geom) return PIPE_EINVAL;
@@ -238,6 +242,13 @@ int pipe_green_setup(const pipe_geometry* geom, const pipe_grid* grid, int igf, 
   if (!near_int(2.0 * geom->x0 / grid->hx, &sx) || !near_int(2.0 * geom->y0 / grid->hy, &sy))
     return PIPE_EUNSUPPORTED;
 
+  if (n_nb >= 0) {
+    // the banded form: n-point transverse routine (cell-centred meshes), planes
+    // paired along z, the nx*ny plane buffer in shared memory
+    if (n_nb >= grid->nz) return PIPE_EINVAL;
+    if (sx != 1 || sy != 1) return PIPE_EUNSUPPORTED;
+    if (cplx_size(grid->dtype) * grid->nx * grid->ny > 200 * 1024) return PIPE_EUNSUPPORTED;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return PIPE_ENODEVICE;
   pipe_handle* h = new (std::nothrow) pipe_handle();
@@ -249,7 +260,9 @@ int pipe_green_setup(const pipe_geometry* geom, const pipe_grid* grid, int igf, 
   h->sx = sx;
   h->sy = sy;
   h->images = 1;
+  h->banded = n_nb;
   h->plan = default_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64, sx == 1 && sy == 1);
+  if (n_nb >= 0) h->plan.t_threads = 256;
   h->free_plan = default_free_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
   if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
   GreenSpec s;
@@ -259,9 +272,24 @@ int pipe_green_setup(const pipe_geometry* geom, const pipe_grid* grid, int igf, 
   s.modes_m = geom->modes_m; s.modes_n = geom->modes_n;
   s.igf = igf;
   s.scale = grid->hx * grid->hy * grid->hz / (8.0 * grid->nx * grid->ny * grid->nz);
-  cudaError_t e = build_pipe_spectrum(s, h->green64, h->green32, nullptr);
+  if (n_nb >= 0) {                       // 2-D spectra of the offsets 0..n_nb
+    s.nz = n_nb;
+    s.scale = grid->hx * grid->hy * grid->hz / (4.0 * grid->nx * grid->ny);
+  }
+  cudaError_t e = build_pipe_spectrum(s, h->green64, h->green32, nullptr, n_nb < 0);
   if (e != cudaSuccess) { free_handle(h); return status_of(e); }
   return finish_setup(h, out);
+}
+
+int pipe_green_setup(const pipe_geometry* geom, const pipe_grid* grid, int igf, pipe_handle** out) {
+  return setup_pipe(geom, grid, igf, -1, out);
+}
+
+int pipe_banded_setup(const pipe_geometry* geom, const pipe_grid* grid, int igf, int n_neighbors,
+                      pipe_handle** out) {
+  if (out) *out = nullptr;
+  if (n_neighbors < 0) return PIPE_EINVAL;
+  return setup_pipe(geom, grid, igf, n_neighbors, out);
 }
 
 int pipe_free_space_setup(const pipe_grid* grid, double self_value, pipe_handle** out) {
@@ -336,7 +364,8 @@ int pipe_poisson_solve_host(pipe_handle* h, const void* rho_host, void* phi_host
 
 int pipe_green_spectrum(pipe_handle* h, double* out, size_t count) {
   if (!h || !out) return PIPE_EINVAL;
-  const size_t oct = size_t(h->grid.nx + 1) * (h->grid.ny + 1) * (h->grid.nz + 1);
+  const int planes = h->banded >= 0 ? h->banded + 1 : h->grid.nz + 1;
+  const size_t oct = size_t(h->grid.nx + 1) * (h->grid.ny + 1) * planes;
   if (count != oct) return PIPE_EINVAL;
   DeviceGuard dg(h->device);
   return status_of(cudaMemcpy(out, h->green64, oct * sizeof(double), cudaMemcpyDeviceToHost));
@@ -344,6 +373,7 @@ int pipe_green_spectrum(pipe_handle* h, double* out, size_t count) {
 
 int pipe_stage_z_forward(pipe_handle* h, const void* rho, void* spec, int adjoint, void* stream) {
   if (!h) return PIPE_EINVAL;
+  if (h->banded >= 0) return PIPE_EUNSUPPORTED;      // no z spectrum in the banded form
   int st;
   if ((st = check_ptr(rho)) != PIPE_OK || (st = check_ptr(spec)) != PIPE_OK) return st;
   DeviceGuard dg(h->device);
@@ -358,6 +388,7 @@ int pipe_stage_z_forward(pipe_handle* h, const void* rho, void* spec, int adjoin
 
 int pipe_stage_transverse(pipe_handle* h, void* spec, int adjoint, void* stream) {
   if (!h) return PIPE_EINVAL;
+  if (h->banded >= 0) return PIPE_EUNSUPPORTED;      // no z spectrum in the banded form
   int st;
   if ((st = check_ptr(spec)) != PIPE_OK) return st;
   DeviceGuard dg(h->device);
@@ -372,6 +403,7 @@ int pipe_stage_transverse(pipe_handle* h, void* spec, int adjoint, void* stream)
 
 int pipe_stage_z_inverse(pipe_handle* h, const void* spec, void* phi, int adjoint, void* stream) {
   if (!h) return PIPE_EINVAL;
+  if (h->banded >= 0) return PIPE_EUNSUPPORTED;      // no z spectrum in the banded form
   int st;
   if ((st = check_ptr(spec)) != PIPE_OK || (st = check_ptr(phi)) != PIPE_OK) return st;
   DeviceGuard dg(h->device);

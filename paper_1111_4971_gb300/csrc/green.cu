@@ -215,7 +215,7 @@ static inline unsigned nblk(long total, int bs) { return unsigned((total + bs - 
 // Forward transform of an even real octant table T (in place through `tmp`):
 // DCT-I along x (p), then y (q), then z (r).  Result in T.
 static cudaError_t octant_transform(double* T, double* tmp, double* cosbuf, int nx, int ny, int nz,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, bool transform_z = true) {
   const long sx = 1, sy = nx + 1, sz = long(nx + 1) * (ny + 1);
   // x axis: lines = q (stride sy), batches = r (stride sz)
   cos_pi_table_kernel<<<nblk(2 * nx, 256), 256, 0, st>>>(cosbuf, nx);
@@ -229,6 +229,7 @@ static cudaError_t octant_transform(double* T, double* tmp, double* cosbuf, int 
     dim3 grid(nblk(nx + 1, 64), nblk(ny + 1, 64), nz + 1);
     dct1_axis_kernel<<<grid, 256, 0, st>>>(tmp, T, ny, nx + 1, sy, 1, sz, cosbuf);
   }
+  if (!transform_z) return cudaGetLastError();               // result in T
   // z axis: lines = (q, p) flattened (stride 1), one batch
   cos_pi_table_kernel<<<nblk(2 * nz, 256), 256, 0, st>>>(cosbuf, nz);
   {
@@ -238,7 +239,8 @@ static cudaError_t octant_transform(double* T, double* tmp, double* cosbuf, int 
   return cudaMemcpyAsync(T, tmp, sizeof(double) * sz * (nz + 1), cudaMemcpyDeviceToDevice, st);
 }
 
-cudaError_t build_pipe_spectrum(const GreenSpec& s, double* g64, float* g32, cudaStream_t st) {
+cudaError_t build_pipe_spectrum(const GreenSpec& s, double* g64, float* g32, cudaStream_t st,
+                                bool transform_z) {
   const int nx = s.nx, ny = s.ny, nz = s.nz, M = s.modes_m, N = s.modes_n;
   const long oct = long(nx + 1) * (ny + 1) * (nz + 1);
   double *cx = nullptr, *cy = nullptr, *Z = nullptr, *U = nullptr, *T = nullptr, *tmp = nullptr,
@@ -261,7 +263,7 @@ cudaError_t build_pipe_spectrum(const GreenSpec& s, double* g64, float* g32, cud
   contract_m_kernel<<<nblk(oct, 256), 256, 0, st>>>(T, cx, U, M, nx, ny, nz,
                                                     2.0 * M_PI / (s.a * s.b));
   if ((err = cudaGetLastError()) != cudaSuccess) goto done;
-  if ((err = octant_transform(T, tmp, cosbuf, nx, ny, nz, st)) != cudaSuccess) goto done;
+  if ((err = octant_transform(T, tmp, cosbuf, nx, ny, nz, st, transform_z)) != cudaSuccess) goto done;
   finalize_kernel<<<nblk(oct, 256), 256, 0, st>>>(T, g64, g32, oct, s.scale);
   if ((err = cudaGetLastError()) != cudaSuccess) goto done;
   err = cudaStreamSynchronize(st);

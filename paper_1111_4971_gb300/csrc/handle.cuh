@@ -23,6 +23,7 @@ struct pipe_handle {
   pipe_geometry geom{};
   pipe_grid grid{};
   int kind = 0;          // 0 ordinary, 1 IGF, 2 free space
+  int banded = -1;       // >= 0: the banded reduction with this many neighbour planes
   int sx = 0, sy = 0;    // correlation shifts 2*x0/hx, 2*y0/hy
   int images = 1;        // four-term pipe operator (1) or free space (0)
   double* green64 = nullptr;

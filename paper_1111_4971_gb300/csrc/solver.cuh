@@ -107,6 +107,9 @@ template <typename T>
 cudaError_t launch_z(bool forward, int warps, int pipe, bool conj, const SolveArgs<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_transverse(bool adjoint, int h, int threads, const SolveArgs<T>& a, cudaStream_t st);
+// banded z reduction (Eq. 17-18): two kernels on `work` as [nz/2][ny][nx]
+template <typename T>
+cudaError_t launch_banded(int threads, const SolveArgs<T>& a, int n_nb, cudaStream_t st);
 template <typename T>
 cudaError_t launch_transverse_sym(bool adjoint, int kind, int hb, int threads, const SolveArgs<T>& a,
                                   cudaStream_t st);

@@ -143,6 +143,18 @@ int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
   Plan best = h->images ? h->plan : h->free_plan;
   float bz = 1e30f, bt = 1e30f;
   const int reps = 5;
+  if (h->banded >= 0) {                 // the banded form: only its CTA size
+    for (int th : {128, 256, 512}) {
+      float ms = time_ms([&] { return launch_banded<T>(th, a, h->banded, st); }, st, reps);
+      if (ms > 0 && ms < bt) { bt = ms; best.t_threads = th; }
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(rho);
+    cudaFree(phi);
+    if (bt > 1e29f) return PIPE_ECUDA;
+    *out = best;
+    return PIPE_OK;
+  }
   for (int zw : {8, 16})
     for (int zp : {0, 1}) {
       float ms = time_ms([&] {
@@ -184,7 +196,9 @@ using namespace pp;
 
 extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
   if (!h) return PIPE_EINVAL;
-  const Key k(h->grid.nx, h->grid.nz, h->grid.dtype + (h->images ? 0 : 2));
+  // banded handles are keyed by their neighbour count as well
+  const Key k(h->grid.nx, h->grid.nz,
+              h->grid.dtype + (h->images ? 0 : 2) + (h->banded >= 0 ? 4 * (h->banded + 1) : 0));
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_file_cache();

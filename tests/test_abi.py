@@ -90,3 +90,20 @@ def test_null_handle_and_pointers(L):
     assert L.pipe_poisson_solve_host(None, None, None, None) == _lib.PIPE_EINVAL
     assert L.pipe_green_spectrum(None, None, 0) == _lib.PIPE_EINVAL
     L.pipe_green_destroy(None)
+
+
+def test_banded_setup_validation_without_gpu(L):
+    G, P = _lib.PipeGeometry, _lib.PipeGrid
+    cc = G(1.0, 1.0, 0.5 / 128, 0.5 / 128, 20, 20)
+    good = P(128, 128, 256, 1 / 128, 1 / 128, 0.1, 0)
+    cases = [
+        (cc, good, -1, _lib.PIPE_EINVAL),                                  # negative band
+        (cc, good, 256, _lib.PIPE_EINVAL),                                 # band >= nz
+        (G(1.0, 1.0, 0.0, 0.0, 20, 20), good, 1, _lib.PIPE_EUNSUPPORTED),  # x0 = 0: s = 0
+        (cc, P(128, 128, 256, 1 / 128, 1 / 128, 0.1, 1), 1, _lib.PIPE_EUNSUPPORTED),  # FP64 128^2
+    ]
+    for geo, grid, n_nb, want in cases:
+        h = ctypes.c_void_p()
+        st = L.pipe_banded_setup(ctypes.byref(geo), ctypes.byref(grid), 1, n_nb, ctypes.byref(h))
+        assert st == want, (n_nb, st)
+        assert not h.value
