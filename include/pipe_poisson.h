@@ -52,6 +52,16 @@ extern "C" {
 /* dtypes */
 #define PIPE_F32 0
 #define PIPE_F64 1
+/* FP32 arithmetic with the z half-spectrum stored between the kernels as
+ * complex FP16 (2 x 16 bits per value) with per-slab FP32 scale factors: one
+ * per z-transform tile of columns after the forward z transform, one per
+ * transverse row after the transverse stage; the Green product is taken in
+ * FP16 on operands scaled per transverse column.  An optional variant whose
+ * error (about 1e-3 relative, FP16 rounding 2^-11) is above the FP32 path's
+ * 1e-5: for uses whose error budget allows it.  Cell-centred meshes only;
+ * solves, adjoints and host solves; not the stage, no-alloc, batched or
+ * banded entry points (PIPE_EUNSUPPORTED).  Fields are FP32 tensors. */
+#define PIPE_F32_C16 2
 
 /* Green function kinds for pipe_green_setup's `igf` argument */
 #define PIPE_GREEN_ORDINARY 0   /* Eq. 9: exp(-kappa |w|) */
@@ -66,7 +76,7 @@ typedef struct {
 } pipe_geometry;
 
 /* Physical mesh nx x ny x nz with spacings hx, hy, hz, and the arithmetic type
- * of the solve (PIPE_F32 or PIPE_F64).  The Green function is always tabulated
+ * of the solve (PIPE_F32, PIPE_F64 or PIPE_F32_C16).  The Green function is always tabulated
  * and transformed in FP64; the F32 path uses an FP32 copy of its spectrum. */
 typedef struct {
   int nx, ny, nz;

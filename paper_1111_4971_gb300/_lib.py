@@ -22,6 +22,7 @@ PIPE_ETIMEOUT = 5
 PIPE_ENODEVICE = 6
 PIPE_F32 = 0
 PIPE_F64 = 1
+PIPE_F32_C16 = 2          # FP32 arithmetic, complex-FP16 spectra with per-slab scales
 
 
 class PipeGeometry(ctypes.Structure):

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 
 #include "../../include/pipe_poisson.h"
 #include "green_kernels.cuh"
@@ -51,7 +52,7 @@ int validate_grid(const pipe_grid* g) {
   if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return PIPE_EINVAL;
   if (!(g->hx > 0) || !(g->hy > 0) || !(g->hz > 0)) return PIPE_EINVAL;
   if (!std::isfinite(g->hx) || !std::isfinite(g->hy) || !std::isfinite(g->hz)) return PIPE_EINVAL;
-  if (g->dtype != PIPE_F32 && g->dtype != PIPE_F64) return PIPE_EINVAL;
+  if (g->dtype != PIPE_F32 && g->dtype != PIPE_F64 && g->dtype != PIPE_F32_C16) return PIPE_EINVAL;
   if (!is_pow2(g->nx) || !is_pow2(g->ny) || !is_pow2(g->nz)) return PIPE_EUNSUPPORTED;
   if (g->nx != g->ny) return PIPE_EUNSUPPORTED;
   if (g->nx < 16 || g->nx > 128) return PIPE_EUNSUPPORTED;
@@ -119,7 +120,7 @@ SolveArgs<T> make_args(pipe_handle* h, const void* rho, void* phi, void* work);
 
 template <>
 SolveArgs<float> make_args<float>(pipe_handle* h, const void* rho, void* phi, void* work) {
-  SolveArgs<float> a;
+  SolveArgs<float> a{};
   a.rho = static_cast<const float*>(rho); a.phi = static_cast<float*>(phi);
   a.work = static_cast<float2*>(work); a.green = h->green32;
   a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32;
@@ -127,11 +128,18 @@ SolveArgs<float> make_args<float>(pipe_handle* h, const void* rho, void* phi, vo
   a.tw_t2c = h->tw_t2c_32;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  if (h->grid.dtype == PIPE_F32_C16) {
+    // work: (nz+1) nx ny complex-FP16 values, then the two scale tables
+    const size_t nodes = size_t(h->grid.nx) * h->grid.ny;
+    a.zscale = reinterpret_cast<float*>(static_cast<char*>(work) + (h->grid.nz + 1) * nodes * 4);
+    a.tscale = a.zscale + nodes;
+    a.zcols = z_tile_cols(h->grid.nz, h->plan.z_warps);
+  }
   return a;
 }
 template <>
 SolveArgs<double> make_args<double>(pipe_handle* h, const void* rho, void* phi, void* work) {
-  SolveArgs<double> a;
+  SolveArgs<double> a{};
   a.rho = static_cast<const double*>(rho); a.phi = static_cast<double*>(phi);
   a.work = static_cast<double2*>(work); a.green = h->green64;
   a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64;
@@ -155,6 +163,15 @@ int run_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStre
   cudaError_t e;
   // the banded operator is symmetric: the adjoint is the same computation
   if (h->banded >= 0) return status_of(launch_banded<T>(h->plan.t_threads, a, h->banded, st));
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->grid.dtype == PIPE_F32_C16) {
+      const int zw = h->plan.z_warps;
+      if ((e = launch_z_c16(true, zw, adjoint, a, st)) != cudaSuccess) return status_of(e);
+      if ((e = launch_transverse_c16(adjoint, h->plan.t_threads, a, st)) != cudaSuccess) return status_of(e);
+      if ((e = launch_z_c16(false, zw, adjoint, a, st)) != cudaSuccess) return status_of(e);
+      return PIPE_OK;
+    }
+  }
   const int zw = h->plan.z_warps, zp = h->plan.z_pipe;
   if ((e = launch_z<T>(true, zw, zp, adjoint, a, st)) != cudaSuccess) return status_of(e);
   if ((e = transverse_stage<T>(h, adjoint, a, st)) != cudaSuccess) return status_of(e);
@@ -242,6 +259,7 @@ static int setup_pipe(const pipe_geometry* geom, const pipe_grid* grid, int igf,
   if (!near_int(2.0 * geom->x0 / grid->hx, &sx) || !near_int(2.0 * geom->y0 / grid->hy, &sy))
     return PIPE_EUNSUPPORTED;
 
+  if (grid->dtype == PIPE_F32_C16 && (sx != 1 || sy != 1 || n_nb >= 0)) return PIPE_EUNSUPPORTED;
   if (n_nb >= 0) {
     // the banded form: n-point transverse routine (cell-centred meshes), planes
     // paired along z, the nx*ny plane buffer in shared memory
@@ -373,7 +391,7 @@ int pipe_green_spectrum(pipe_handle* h, double* out, size_t count) {
 
 int pipe_stage_z_forward(pipe_handle* h, const void* rho, void* spec, int adjoint, void* stream) {
   if (!h) return PIPE_EINVAL;
-  if (h->banded >= 0) return PIPE_EUNSUPPORTED;      // no z spectrum in the banded form
+  if (h->banded >= 0 || h->grid.dtype == PIPE_F32_C16) return PIPE_EUNSUPPORTED;      // no z spectrum in the banded form
   int st;
   if ((st = check_ptr(rho)) != PIPE_OK || (st = check_ptr(spec)) != PIPE_OK) return st;
   DeviceGuard dg(h->device);
@@ -388,7 +406,7 @@ int pipe_stage_z_forward(pipe_handle* h, const void* rho, void* spec, int adjoin
 
 int pipe_stage_transverse(pipe_handle* h, void* spec, int adjoint, void* stream) {
   if (!h) return PIPE_EINVAL;
-  if (h->banded >= 0) return PIPE_EUNSUPPORTED;      // no z spectrum in the banded form
+  if (h->banded >= 0 || h->grid.dtype == PIPE_F32_C16) return PIPE_EUNSUPPORTED;      // no z spectrum in the banded form
   int st;
   if ((st = check_ptr(spec)) != PIPE_OK) return st;
   DeviceGuard dg(h->device);
@@ -403,7 +421,7 @@ int pipe_stage_transverse(pipe_handle* h, void* spec, int adjoint, void* stream)
 
 int pipe_stage_z_inverse(pipe_handle* h, const void* spec, void* phi, int adjoint, void* stream) {
   if (!h) return PIPE_EINVAL;
-  if (h->banded >= 0) return PIPE_EUNSUPPORTED;      // no z spectrum in the banded form
+  if (h->banded >= 0 || h->grid.dtype == PIPE_F32_C16) return PIPE_EUNSUPPORTED;      // no z spectrum in the banded form
   int st;
   if ((st = check_ptr(spec)) != PIPE_OK || (st = check_ptr(phi)) != PIPE_OK) return st;
   DeviceGuard dg(h->device);

@@ -18,6 +18,8 @@
 // is normalised (the solver folds every 1/L into the Green spectrum).
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <type_traits>

@@ -26,6 +26,12 @@ struct SolveArgs {
   int nx, ny, nz;
   int sx, sy;        // correlation shifts 2*x0/hx, 2*y0/hy (integers)
   int images;        // 1: four-term pipe operator, 0: free-space (one term)
+  // complex-FP16 spectra (PIPE_F32_C16 handles only): `work` then holds
+  // __half2 values with per-slab FP32 scales, zscale[tile] for the z-forward
+  // tiles of zcols columns and tscale[kz * nx + i] for the transverse rows
+  float* zscale;
+  float* tscale;
+  int zcols;
 };
 
 // z transforms: one CTA handles COLS consecutive (i,j) columns.
@@ -56,9 +62,9 @@ struct ZCfg {
   static constexpr size_t inv_pipe_smem() { return sizeof(C2<T>) * (2 * STG + SCR); }
 };
 
-template <typename T, int NZ, int WARPS, bool CONJ>
+template <typename T, int NZ, int WARPS, bool CONJ, bool H16 = false>
 __global__ void zfwd_kernel(SolveArgs<T> a);
-template <typename T, int NZ, int WARPS, bool CONJ>
+template <typename T, int NZ, int WARPS, bool CONJ, bool H16 = false>
 __global__ void zinv_kernel(SolveArgs<T> a);
 
 // transverse stage: one cluster of 2*H CTAs per kz plane, THREADS per CTA.
@@ -107,6 +113,12 @@ template <typename T>
 cudaError_t launch_z(bool forward, int warps, int pipe, bool conj, const SolveArgs<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_transverse(bool adjoint, int h, int threads, const SolveArgs<T>& a, cudaStream_t st);
+// complex-FP16 spectra with FP32 arithmetic (single-tile z kernels, n-point
+// transverse routine); z_tile_cols gives the z-forward tile width (the slab
+// of its scales) for nz and the CTA size in warps
+cudaError_t launch_z_c16(bool forward, int warps, bool conj, const SolveArgs<float>& a, cudaStream_t st);
+cudaError_t launch_transverse_c16(bool adjoint, int threads, const SolveArgs<float>& a, cudaStream_t st);
+int z_tile_cols(int nz, int warps);
 // banded z reduction (Eq. 17-18): two kernels on `work` as [nz/2][ny][nx]
 template <typename T>
 cudaError_t launch_banded(int threads, const SolveArgs<T>& a, int n_nb, cudaStream_t st);

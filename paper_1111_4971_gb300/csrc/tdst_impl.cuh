@@ -55,7 +55,11 @@ __device__ __forceinline__ V cfma_(V a, V w, V b) {
   return mk<V>(a.x + (w.x * b.x - w.y * b.y), a.y + (w.x * b.y + w.y * b.x));
 }
 
-template <typename T, int N, int THREADS, bool ADJ>
+// H16 (complex-FP16 spectra, FP32 arithmetic): the plane is read as __half2
+// with the z-forward tile scales, the Green product is taken in FP16 with one
+// scale per column for each operand, and the result is stored as __half2
+// with one scale per row (a.tscale).
+template <typename T, int N, int THREADS, bool ADJ, bool H16 = false>
 struct TDst {
   using Cfg = TDstCfg<T, N, THREADS>;
   using V = C2<T>;
@@ -102,6 +106,28 @@ struct TDst {
     }
   }
 
+  // max over the G lanes of one group (consecutive lanes)
+  __device__ static __forceinline__ float group_max(float x) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+  }
+
+  // load_row for complex-FP16 planes: values times their z-tile scale
+  __device__ __forceinline__ void load_row16(const SolveArgs<T>& a, int kz, int il, V (&v)[E]) const {
+    const int i = il < N ? il : 0;
+    const __half2* row = reinterpret_cast<const __half2*>(a.work) + (size_t(kz) * N + i) * N;
+    const float* zs = a.zscale;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int n = t + G * e;
+      const int j = e < H ? 2 * n : 2 * N - 1 - 2 * n;
+      const float2 f = __half22float2(row[j]);
+      const float sc = __ldg(&zs[(i * N + j) / a.zcols]) * (e < H ? 1.f : -1.f);
+      v[e] = mk<V>(T(f.x * sc), T(f.y * sc));
+    }
+  }
+
   // the phase table; the caller synchronises before the first plane
   __device__ __forceinline__ void load_tables(const SolveArgs<T>& a) {
     for (int i = threadIdx.x; i < 2 * N; i += THREADS) sw2[i] = a.w2_t[i];
@@ -118,7 +144,8 @@ struct TDst {
     for (int r0 = 0; r0 < N; r0 += GPC) {
       const int il = r0 + line;
       V v[E];
-      load_row(pl, il, v);
+      if constexpr (H16) load_row16(a, kz, il, v);
+      else load_row(pl, il, v);
       group_fft<N, INV1>(v, scratch, tw, t);                   // V(q)
       V m[E];
       mirror_fetch<N>(v, m, t, 0, lane - t);                   // V(N-q)
@@ -154,14 +181,41 @@ struct TDst {
       V m[E];
       mirror_fetch<N>(u, m, t, 0, lane - t);
       const T* grow = a.green + (size_t(kz) * (N + 1) + ky) * (N + 1);
+      if constexpr (!H16) {
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int kx = t + G * e;
-        const T g = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
-        // slot 0 carries kx = N: U(N) = 2 V(0)
-        const V w = (kx == 0) ? mk<V>(u[e].x + u[e].x, u[e].y + u[e].y)
-                              : cfms(u[e], sw2[(SGN * kx) & MASK], m[e]);
-        u[e] = cscale(w, g);                                   // P(kx)
+        for (int e = 0; e < E; ++e) {
+          const int kx = t + G * e;
+          const T g = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
+          // slot 0 carries kx = N: U(N) = 2 V(0)
+          const V w = (kx == 0) ? mk<V>(u[e].x + u[e].x, u[e].y + u[e].y)
+                                : cfms(u[e], sw2[(SGN * kx) & MASK], m[e]);
+          u[e] = cscale(w, g);                                 // P(kx)
+        }
+      } else {
+        // complex-FP16 product: both operands scaled per column so that
+        // their largest magnitude is 2^7 (the product stays below 2^14)
+        float g[E];
+        float mu = 0.f, mg = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int kx = t + G * e;
+          g[e] = act ? float(__ldg(&grow[kx == 0 ? N : kx])) : 0.f;
+          u[e] = (kx == 0) ? mk<V>(u[e].x + u[e].x, u[e].y + u[e].y)
+                           : cfms(u[e], sw2[(SGN * kx) & MASK], m[e]);
+          mu = fmaxf(mu, fmaxf(fabsf(float(u[e].x)), fabsf(float(u[e].y))));
+          mg = fmaxf(mg, fabsf(g[e]));
+        }
+        mu = group_max(mu);
+        mg = group_max(mg);
+        const float su = mu > 0.f ? mu * (1.f / 128.f) : 1.f, sg = mg > 0.f ? mg * (1.f / 128.f) : 1.f;
+        const float iu = 1.f / su, ig = 1.f / sg, back = su * sg;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const __half2 uh = __floats2half2_rn(float(u[e].x) * iu, float(u[e].y) * iu);
+          const __half2 ph = __hmul2(uh, __float2half2_rn(g[e] * ig));
+          const float2 pf = __half22float2(ph);
+          u[e] = mk<V>(T(pf.x * back), T(pf.y * back));       // P(kx)
+        }
       }
       mirror_fetch<N>(u, m, t, 0, lane - t);                   // P(N-kx)
 #pragma unroll
@@ -199,7 +253,23 @@ struct TDst {
         }
       }
       group_fft<N, INV2>(u, scratch, tw, t);
-      if (il < N) {
+      if constexpr (H16) {
+        float mx = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) mx = fmaxf(mx, fmaxf(fabsf(float(u[e].x)), fabsf(float(u[e].y))));
+        mx = group_max(mx);
+        const float sc = mx > 0.f ? mx * (1.f / 16384.f) : 1.f, inv = 1.f / sc;
+        if (il < N) {
+          if (t == 0) a.tscale[size_t(kz) * N + i] = sc;
+          __half2* out = reinterpret_cast<__half2*>(a.work) + (size_t(kz) * N + i) * N;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int n = t + G * e;
+            const float sg = e < H ? inv : -inv;
+            out[e < H ? 2 * n : 2 * N - 1 - 2 * n] = __floats2half2_rn(float(u[e].x) * sg, float(u[e].y) * sg);
+          }
+        }
+      } else if (il < N) {
         V* out = pl + size_t(i) * N;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -213,9 +283,9 @@ struct TDst {
 };
 
 // one plane
-template <typename T, int N, int THREADS, bool ADJ>
+template <typename T, int N, int THREADS, bool ADJ, bool H16 = false>
 __device__ __forceinline__ void tdst_plane(const SolveArgs<T>& a, int kz, unsigned char* smem_raw) {
-  TDst<T, N, THREADS, ADJ> r(a, smem_raw);
+  TDst<T, N, THREADS, ADJ, H16> r(a, smem_raw);
   r.load_tables(a);
   __syncthreads();
   r.plane(a, kz);

@@ -66,20 +66,20 @@ static cudaError_t tclaunch(const SolveArgs<T>& a, cudaStream_t st) {
 }
 
 // the N-point routine for cell-centred meshes: one CTA per kz plane
-template <typename T, int N, int THREADS, bool ADJ>
+template <typename T, int N, int THREADS, bool ADJ, bool H16 = false>
 __global__ void __launch_bounds__(THREADS, 1) transverse_dst_kernel(SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  tdst_plane<T, N, THREADS, ADJ>(a, blockIdx.x, smem_raw);
+  tdst_plane<T, N, THREADS, ADJ, H16>(a, blockIdx.x, smem_raw);
 }
 
-template <typename T, int N, int THREADS, bool ADJ>
+template <typename T, int N, int THREADS, bool ADJ, bool H16 = false>
 static cudaError_t tdlaunch(const SolveArgs<T>& a, cudaStream_t st) {
   using Cfg = TDstCfg<T, N, THREADS>;
   if constexpr (Cfg::smem_bytes() > kMaxSmem) {
     return cudaErrorInvalidConfiguration;
   } else {
     const size_t smem = Cfg::smem_bytes();
-    void (*kern)(SolveArgs<T>) = transverse_dst_kernel<T, N, THREADS, ADJ>;
+    void (*kern)(SolveArgs<T>) = transverse_dst_kernel<T, N, THREADS, ADJ, H16>;
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
@@ -144,5 +144,28 @@ cudaError_t launch_transverse_sym<PP_TS_TYPE>(bool adjoint, int kind, int hb, in
     default: return cudaErrorInvalidValue;
   }
 }
+
+#if !defined(PP_TS_F64_UNIT)
+template <int N>
+static cudaError_t tdlaunch16(bool adjoint, int threads, const SolveArgs<float>& a, cudaStream_t st) {
+  switch (threads) {
+    case 128: return adjoint ? tdlaunch<float, N, 128, true, true>(a, st) : tdlaunch<float, N, 128, false, true>(a, st);
+    case 256: return adjoint ? tdlaunch<float, N, 256, true, true>(a, st) : tdlaunch<float, N, 256, false, true>(a, st);
+    case 512: return adjoint ? tdlaunch<float, N, 512, true, true>(a, st) : tdlaunch<float, N, 512, false, true>(a, st);
+    default: return cudaErrorInvalidConfiguration;
+  }
+}
+
+cudaError_t launch_transverse_c16(bool adjoint, int threads, const SolveArgs<float>& a, cudaStream_t st) {
+  if (a.nx != a.ny || !a.images || a.sx != 1 || a.sy != 1 || a.zcols <= 0) return cudaErrorInvalidValue;
+  switch (a.nx) {
+    case 16: return tdlaunch16<16>(adjoint, threads, a, st);
+    case 32: return tdlaunch16<32>(adjoint, threads, a, st);
+    case 64: return tdlaunch16<64>(adjoint, threads, a, st);
+    case 128: return tdlaunch16<128>(adjoint, threads, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+#endif
 
 }  // namespace pp

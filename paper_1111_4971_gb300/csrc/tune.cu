@@ -90,7 +90,7 @@ template <typename T>
 SolveArgs<T> args_for(pipe_handle* h, void* rho, void* phi);
 template <>
 SolveArgs<float> args_for<float>(pipe_handle* h, void* rho, void* phi) {
-  SolveArgs<float> a;
+  SolveArgs<float> a{};
   a.rho = static_cast<const float*>(rho); a.phi = static_cast<float*>(phi);
   a.work = static_cast<float2*>(h->work); a.green = h->green32;
   a.tw_t = h->tw_t32; a.w2_t = h->w2_t32; a.tw_z = h->tw_z32; a.w2_z = h->w2_z32;
@@ -102,7 +102,7 @@ SolveArgs<float> args_for<float>(pipe_handle* h, void* rho, void* phi) {
 }
 template <>
 SolveArgs<double> args_for<double>(pipe_handle* h, void* rho, void* phi) {
-  SolveArgs<double> a;
+  SolveArgs<double> a{};
   a.rho = static_cast<const double*>(rho); a.phi = static_cast<double*>(phi);
   a.work = static_cast<double2*>(h->work); a.green = h->green64;
   a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64;
@@ -196,6 +196,7 @@ using namespace pp;
 
 extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
   if (!h) return PIPE_EINVAL;
+  if (h->grid.dtype == PIPE_F32_C16) return PIPE_OK;     // fixed variant: nothing to choose
   // banded handles are keyed by their neighbour count as well
   const Key k(h->grid.nx, h->grid.nz,
               h->grid.dtype + (h->images ? 0 : 2) + (h->banded >= 0 ? 4 * (h->banded + 1) : 0));

@@ -4,16 +4,16 @@
 
 namespace pp {
 
-template <typename T, int NZ, int WARPS, bool CONJ>
+template <typename T, int NZ, int WARPS, bool CONJ, bool H16>
 __global__ void __launch_bounds__(32 * WARPS, (WARPS <= 8 ? 2 : 1)) zfwd_kernel(SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  zfwd_tile<T, NZ, WARPS, CONJ>(a, blockIdx.x, smem_raw);
+  zfwd_tile<T, NZ, WARPS, CONJ, H16>(a, blockIdx.x, smem_raw);
 }
 
-template <typename T, int NZ, int WARPS, bool CONJ>
+template <typename T, int NZ, int WARPS, bool CONJ, bool H16>
 __global__ void __launch_bounds__(32 * WARPS, (WARPS <= 8 ? 2 : 1)) zinv_kernel(SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  zinv_tile<T, NZ, WARPS, CONJ>(a, blockIdx.x, smem_raw);
+  zinv_tile<T, NZ, WARPS, CONJ, H16>(a, blockIdx.x, smem_raw);
 }
 
 // pipelined variants: a grid of at most (SMs x resident CTAs), each CTA
@@ -112,5 +112,54 @@ cudaError_t launch_z<PP_Z_TYPE>(bool forward, int warps, int pipe, bool conj, co
     default: return cudaErrorInvalidValue;
   }
 }
+
+#if !defined(PP_Z_F64_UNIT)
+// complex-FP16 spectra (FP32 arithmetic): single-tile kernels only
+template <int NZ, int W, bool C>
+static cudaError_t zlaunch16(bool forward, const SolveArgs<float>& a, cudaStream_t st) {
+  using Cfg = ZCfg<float, NZ, W>;
+  const size_t smem = Cfg::smem_bytes() + sizeof(float) * W;      // + the tile-max scratch
+  if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
+  void (*kern)(SolveArgs<float>) = forward ? zfwd_kernel<float, NZ, W, C, true> : zinv_kernel<float, NZ, W, C, true>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  const int ncols = a.nx * a.ny;
+  kern<<<(ncols + Cfg::COLS - 1) / Cfg::COLS, Cfg::THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NZ, int W>
+static cudaError_t zlaunch16c(bool forward, bool conj, const SolveArgs<float>& a, cudaStream_t st) {
+  return conj ? zlaunch16<NZ, W, true>(forward, a, st) : zlaunch16<NZ, W, false>(forward, a, st);
+}
+
+cudaError_t launch_z_c16(bool forward, int warps, bool conj, const SolveArgs<float>& a, cudaStream_t st) {
+  const bool w16 = (warps == 16);
+  switch (a.nz) {
+    case 32: return zlaunch16c<32, 8>(forward, conj, a, st);
+    case 64: return zlaunch16c<64, 8>(forward, conj, a, st);
+    case 128: return zlaunch16c<128, 8>(forward, conj, a, st);
+    case 256: return zlaunch16c<256, 8>(forward, conj, a, st);
+    case 512: return w16 ? zlaunch16c<512, 16>(forward, conj, a, st) : zlaunch16c<512, 8>(forward, conj, a, st);
+    case 1024: return w16 ? zlaunch16c<1024, 16>(forward, conj, a, st) : zlaunch16c<1024, 8>(forward, conj, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int z_tile_cols(int nz, int warps) {
+  const bool w16 = (warps == 16);
+  switch (nz) {
+    case 32: return ZCfg<float, 32, 8>::COLS;
+    case 64: return ZCfg<float, 64, 8>::COLS;
+    case 128: return ZCfg<float, 128, 8>::COLS;
+    case 256: return ZCfg<float, 256, 8>::COLS;
+    case 512: return w16 ? ZCfg<float, 512, 16>::COLS : ZCfg<float, 512, 8>::COLS;
+    case 1024: return w16 ? ZCfg<float, 1024, 16>::COLS : ZCfg<float, 1024, 8>::COLS;
+    default: return 0;
+  }
+}
+#endif
 
 }  // namespace pp

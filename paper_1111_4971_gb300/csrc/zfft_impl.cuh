@@ -32,6 +32,16 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
+// asynchronous 4-byte global -> shared copy
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// largest component of a complex-FP16 slab is stored as 2^14 (headroom below
+// the FP16 maximum 65504); an all-zero slab keeps scale 1
+__device__ __forceinline__ float slab_scale(float mx) { return mx > 0.f ? mx * (1.f / 16384.f) : 1.f; }
+
 // asynchronous 8-byte global -> shared copy
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
@@ -50,7 +60,9 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // one CTA of 32*WARPS threads: columns [tile*COLS, (tile+1)*COLS)
-template <typename T, int NZ, int WARPS, bool CONJ>
+// H16: the spectrum is stored as complex FP16 with one scale per tile
+// (a.zscale[tile]); the reduction scratch follows Cfg::smem_bytes().
+template <typename T, int NZ, int WARPS, bool CONJ, bool H16 = false>
 __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsigned char* smem_raw) {
   using Cfg = ZCfg<T, NZ, WARPS>;
   using V = C2<T>;
@@ -101,6 +113,43 @@ __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsig
 #pragma unroll
   for (int e = 0; e < E; ++e) mycol[2 * (t + G * e) + p] = v[e];
   if (p == 0 && t == 0) mycol[NZ] = CONJ ? cconj(xN) : xN;
+  if constexpr (H16) {
+    float* red = reinterpret_cast<float*>(smem_raw + Cfg::smem_bytes());
+    float mx = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) mx = fmaxf(mx, fmaxf(fabsf(float(v[e].x)), fabsf(float(v[e].y))));
+    if (p == 0 && t == 0) mx = fmaxf(mx, fabsf(float(xN.x)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    mx = 0.f;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) mx = fmaxf(mx, red[w]);
+    const float sc = slab_scale(mx), inv = 1.f / sc;
+    if (threadIdx.x == 0) a.zscale[tile] = sc;
+    // 16-byte stores of four complex-FP16 values (consecutive columns)
+    constexpr int VPR = Cfg::COLS / 4;
+    static_assert(Cfg::COLS % 4 == 0, "tile width");
+    __half2* w16 = reinterpret_cast<__half2*>(a.work);
+    for (int idx = threadIdx.x; idx < (NZ + 1) * VPR; idx += Cfg::THREADS) {
+      const int r = idx / VPR;
+      const int cc = (idx % VPR) * 4;
+      if (col0 + cc < ncols) {
+        union {
+          uint4 u;
+          __half2 h[4];
+        } pk;                                       // 16-byte aligned by its uint4 member
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const V x = stage[(cc + q) * Cfg::LDS + r];
+          pk.h[q] = __floats2half2_rn(float(x.x) * inv, float(x.y) * inv);
+        }
+        *reinterpret_cast<uint4*>(&w16[size_t(r) * ncols + col0 + cc]) = pk.u;
+      }
+    }
+    return;
+  }
   __syncthreads();
   // 16-byte stores: EPV complex (consecutive columns) per vector
   constexpr int EPV = 16 / int(sizeof(V));
@@ -119,7 +168,9 @@ __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsig
   }
 }
 
-template <typename T, int NZ, int WARPS, bool CONJ>
+// H16: the spectrum is complex FP16 with one scale per transverse row
+// (a.tscale[kz * nx + i]; the tile's columns lie in one row i)
+template <typename T, int NZ, int WARPS, bool CONJ, bool H16 = false>
 __device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsigned char* smem_raw) {
   using Cfg = ZCfg<T, NZ, WARPS>;
   using V = C2<T>;
@@ -138,19 +189,44 @@ __device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsig
   const bool valid = col < ncols;
   V* scratch = sbase + (threadIdx.x / G) * GroupShape<L>::SSTRIDE;
 
-  // the whole (nz+1) x COLS tile in flight at once (cp.async, one element each)
-  for (int idx = threadIdx.x; idx < (NZ + 1) * Cfg::COLS; idx += Cfg::THREADS) {
-    const int r = idx / Cfg::COLS;
-    const int cc = idx % Cfg::COLS;
-    if (col0 + cc < ncols) cp_async_elem(&stage[cc * Cfg::LDS + r], &a.work[size_t(r) * ncols + col0 + cc]);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  const V* mycol = stage + col_local * Cfg::LDS;
   V v[E];
+  V xN;
+  if constexpr (H16) {
+    __half2* st16 = reinterpret_cast<__half2*>(smem_raw);
+    const __half2* w16 = reinterpret_cast<const __half2*>(a.work);
+    for (int idx = threadIdx.x; idx < (NZ + 1) * Cfg::COLS; idx += Cfg::THREADS) {
+      const int r = idx / Cfg::COLS;
+      const int cc = idx % Cfg::COLS;
+      if (col0 + cc < ncols) cp_async4(&st16[cc * Cfg::LDS + r], &w16[size_t(r) * ncols + col0 + cc]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const __half2* mycol = st16 + col_local * Cfg::LDS;
+    const float* rs = a.tscale + (valid ? col : 0) / a.ny;     // + kz * nx
 #pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = mycol[2 * (t + G * e) + p];
-  V xN = mycol[NZ];
+    for (int e = 0; e < E; ++e) {
+      const int k = 2 * (t + G * e) + p;
+      const float2 f = __half22float2(mycol[k]);
+      const float sc = __ldg(&rs[size_t(k) * a.nx]);
+      v[e] = mk<V>(T(f.x * sc), T(f.y * sc));
+    }
+    const float2 f = __half22float2(mycol[NZ]);
+    const float sc = __ldg(&rs[size_t(NZ) * a.nx]);
+    xN = mk<V>(T(f.x * sc), T(f.y * sc));
+  } else {
+    // the whole (nz+1) x COLS tile in flight at once (cp.async, one element each)
+    for (int idx = threadIdx.x; idx < (NZ + 1) * Cfg::COLS; idx += Cfg::THREADS) {
+      const int r = idx / Cfg::COLS;
+      const int cc = idx % Cfg::COLS;
+      if (col0 + cc < ncols) cp_async_elem(&stage[cc * Cfg::LDS + r], &a.work[size_t(r) * ncols + col0 + cc]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const V* mycol = stage + col_local * Cfg::LDS;
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = mycol[2 * (t + G * e) + p];
+    xN = mycol[NZ];
+  }
   __syncthreads();                                    // staging tile becomes FFT scratch
   if (CONJ) {
 #pragma unroll
