@@ -258,6 +258,15 @@ int pipe_autotune(pipe_handle* h, void* stream);
 int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h, int* t_threads, int* t_kind);
 int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads, int t_kind);
 
+/* Electric field E = -grad phi on the handle's mesh (device arrays of the
+ * handle's dtype; FP32 for PIPE_F32_C16): phi [nx][ny][nz], E [3][nx][ny][nz]
+ * (x, y, z components, each laid out like phi).  The paper defines no
+ * discrete gradient: second-order central differences inside the mesh,
+ * second-order one-sided differences on its faces (exact for potentials
+ * quadratic in each coordinate).  Asynchronous on `stream`.
+ * Errors: PIPE_EINVAL (null or misaligned pointers), PIPE_ECUDA. */
+int pipe_electric_field(pipe_handle* h, const void* phi, void* E, void* stream);
+
 /* Cloud-in-cell deposit of n macroparticles (positions xyz[n][3], FP64 or FP32
  * per the handle's dtype, charge q each) onto the handle's mesh nodes:
  * rho[i][j][k] += q * w / (hx*hy*hz), w the trilinear weight of node (i,j,k).

@@ -355,6 +355,18 @@ def hockney_spectrum_octant(grid, self_value=None, scaled=True):
     return oct_
 
 
+def electric_field(phi, grid):
+    """E = -grad phi on the mesh (the field a particle-in-cell code gathers).
+
+    The paper gives no discrete gradient; the reading taken is second-order
+    central differences inside the mesh and second-order one-sided
+    differences on its faces, i.e. numpy.gradient with edge_order=2 (exact
+    for potentials quadratic in each coordinate).  Returns E[3][nx][ny][nz].
+    """
+    g = np.gradient(np.asarray(phi, dtype=np.float64), grid.hx, grid.hy, grid.hz, edge_order=2)
+    return -np.stack(g)
+
+
 def field_energy(rho, phi, grid):
     """W = 1/2 sum rho phi (the objective of the differentiable workload)."""
     return 0.5 * float(np.sum(np.asarray(rho) * np.asarray(phi)))

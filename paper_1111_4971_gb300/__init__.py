@@ -164,6 +164,14 @@ class PipeSolver:
         check(self.lib.pipe_set_plan(self.handle, int(z_warps), int(z_pipe), int(t_h), int(t_threads),
                                      int(t_kind)), "pipe_set_plan")
 
+    def electric_field(self, phi: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """E = -grad phi on the mesh, shape (3, nx, ny, nz)."""
+        self._check_field(phi, "phi")
+        out = torch.empty((3,) + self.shape, dtype=self.dtype, device=self.device) if out is None else out
+        check(self.lib.pipe_electric_field(self.handle, _ptr(phi), _ptr(out), _stream_ptr(stream)),
+              "pipe_electric_field")
+        return out
+
     def cic_deposit(self, xyz: torch.Tensor, charge: float, out: torch.Tensor | None = None,
                     stream=None):
         out = torch.zeros(self.shape, dtype=self.dtype, device=self.device) if out is None else out

@@ -47,6 +47,7 @@ SIGNATURES = {
     "pipe_poisson_solve_noalloc": (c_int, [H, c_void_p, c_void_p, c_void_p]),
     "pipe_poisson_solve_batched": (c_int, [POINTER(H), POINTER(c_void_p), POINTER(c_void_p), c_int,
                                            c_void_p]),
+    "pipe_electric_field": (c_int, [H, c_void_p, c_void_p, c_void_p]),
     "pipe_batch_status": (c_int, [POINTER(H), c_int]),
     "pipe_batch_inject_fault": (c_int, [POINTER(H), c_int, c_int, ctypes.c_longlong]),
     "pipe_batch_plan_info": (c_int, [POINTER(H), c_int, POINTER(c_int), POINTER(c_int)]),

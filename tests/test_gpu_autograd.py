@@ -141,3 +141,16 @@ def test_bunch_density_gradient_against_cpu_adjoint():
     want = pipe.direct_sum_at(rho_np, geom, grid, 1, nodes)
     got = np.array([float(g[n]) for n in nodes])
     assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+
+
+def test_electric_field_against_oracle():
+    """E = -grad phi of a solve (the field a particle-in-cell step gathers)."""
+    from paper_1111_4971_gb300 import PipeSolver
+    w = bunches.workload_igf_64()
+    geom, grid, rho = w["geom"], w["grid"], w["rho"][0]
+    for dtype, tol in ((torch.float64, 1e-13), (torch.float32, 1e-5)):
+        s = PipeSolver(geom, grid, igf=True, dtype=dtype)
+        phi = s.solve(torch.tensor(rho, dtype=dtype, device="cuda"))
+        E = s.electric_field(phi).double().cpu().numpy()
+        want = pipe.electric_field(phi.double().cpu().numpy(), grid)
+        assert np.abs(E - want).max() <= tol * np.abs(want).max()

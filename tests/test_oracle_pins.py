@@ -409,3 +409,29 @@ def test_banded_long_bunch_close_to_full():
     e1 = rel(pipe.banded_solve(rho, geom, grid, 1, 1), full)
     assert 1e-3 < e0 < 0.03
     assert e1 < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Field output E = -grad phi: exact for quadratics, second order otherwise
+# ---------------------------------------------------------------------------
+
+def test_electric_field_exact_on_quadratics_and_second_order():
+    grid = Grid(7, 6, 9, 0.3, 0.2, 0.45)
+    x = np.arange(grid.nx)[:, None, None] * grid.hx
+    y = np.arange(grid.ny)[None, :, None] * grid.hy
+    z = np.arange(grid.nz)[None, None, :] * grid.hz
+    phi = 1.5 * x * x - 0.7 * x * y + 2.0 * z * z - 0.3 * y * z + x - 4.0 * y + 0.25
+    E = pipe.electric_field(phi, grid)
+    shape = phi.shape
+    assert np.allclose(E[0], np.broadcast_to(-(3.0 * x - 0.7 * y + 1.0), shape), atol=1e-12)
+    assert np.allclose(E[1], np.broadcast_to(-(-0.7 * x - 0.3 * z - 4.0), shape), atol=1e-12)
+    assert np.allclose(E[2], np.broadcast_to(-(4.0 * z - 0.3 * y), shape), atol=1e-12)
+    # a smooth non-polynomial potential: the error falls by 4 when h halves
+    errs = []
+    for n in (16, 32):
+        g = Grid(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n)
+        t = np.arange(n) / n
+        X, Y, Z = np.meshgrid(t, t, t, indexing="ij")
+        E = pipe.electric_field(np.sin(2 * X) * np.cos(Y) * np.exp(Z), g)
+        errs.append(np.abs(E[0] + 2 * np.cos(2 * X) * np.cos(Y) * np.exp(Z)).max())
+    assert 3.0 < errs[0] / errs[1] < 5.0
