@@ -91,9 +91,13 @@ typedef struct pipe_handle pipe_handle;
  * once, stored, reused).  Allocates every device buffer the solves need.
  *
  * Supported in this build: nx == ny in {16, 32, 64, 128}; nz in
- * {32, 64, 128, 256, 512, 1024}; meshes that span the pipe (nx*hx == a,
- * ny*hy == b to 1e-12 relative) with 2*x0/hx and 2*y0/hy integers (cell-centred
- * x0 = hx/2, or a node on the wall x0 = 0); 1 <= modes <= 4096.
+ * {32, 64, 128, 256, 512, 1024}; 1 <= modes <= 4096.  Meshes that span the
+ * pipe (nx*hx == a, ny*hy == b to 1e-12 relative) with 2*x0/hx and 2*y0/hy
+ * integers (cell-centred x0 = hx/2, or a node on the wall x0 = 0) store one
+ * real octant of the spectrum; any other mesh inside the pipe (a transverse
+ * window, Sec. 5: smaller than the cross-section, at any origin) uses the
+ * general form of Eq. 10 with the four transformed tables stored in full,
+ * for nx == ny <= 64.
  * Errors: PIPE_EINVAL (non-positive sizes or spacings, mesh not inside the
  * pipe, bad dtype / igf, out == NULL), PIPE_EUNSUPPORTED (other sizes or
  * meshes), PIPE_ENOMEM, PIPE_ECUDA.  On error *out is set to NULL.
@@ -216,10 +220,13 @@ int pipe_batch_select(pipe_handle* const* handles, int n, int variant, int order
  * The results of that call are undefined.  Errors: PIPE_EINVAL. */
 int pipe_batch_inject_fault(pipe_handle* const* handles, int n, int drop_stage, long long spin_limit);
 
-/* Copy the handle's FP64 Green spectrum (the real octant g[kz][ky][kx],
- * kz <= nz, ky <= ny, kx <= nx, already multiplied by hx*hy*hz/(8*nx*ny*nz))
- * to host memory `out` of `count` doubles; count must equal
- * (nx+1)*(ny+1)*(nz+1).  Synchronous.  For inspection and tests. */
+/* Copy the handle's FP64 Green spectrum to host memory `out` of `count`
+ * doubles.  Spanning meshes: the real octant g[kz][ky][kx], kz <= nz,
+ * ky <= ny, kx <= nx, already multiplied by hx*hy*hz/(8*nx*ny*nz); count
+ * (nx+1)*(ny+1)*(nz+1).  Window meshes: the four transformed tables
+ * [cc, cr, rc, rr][kz <= nz][ky < 2ny][kx < 2nx] as interleaved complex
+ * (re, im), same scale; count 8*(nz+1)*(2ny)*(2nx).  Banded handles: see
+ * pipe_banded_setup.  Synchronous.  For inspection and tests. */
 int pipe_green_spectrum(pipe_handle* h, double* out, size_t count);
 
 /* Stages of the solve, exposed for inspection and per-kernel tests.  `spec`

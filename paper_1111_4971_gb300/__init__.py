@@ -32,6 +32,15 @@ def _ptr(t: torch.Tensor):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _spans(geometry, grid) -> bool:
+    """The mesh spans the pipe with integer 2*x0/hx, 2*y0/hy (the octant form)."""
+    def near_int(x):
+        return abs(x - round(x)) <= 1e-9 * max(1.0, abs(x))
+    return (abs(grid.nx * grid.hx - geometry.a) <= 1e-12 * geometry.a
+            and abs(grid.ny * grid.hy - geometry.b) <= 1e-12 * geometry.b
+            and near_int(2.0 * geometry.x0 / grid.hx) and near_int(2.0 * geometry.y0 / grid.hy))
+
+
 class PipeSolver:
     """One Green-function setup (Sec. 5: computed once, reused) and its solves.
 
@@ -57,6 +66,9 @@ class PipeSolver:
         self.igf = bool(igf)
         self.free_space = free_space
         self.banded = banded
+        # a mesh that does not span the pipe at integer correlation shifts
+        # (a transverse window) uses the general four-table form
+        self.general = (not free_space) and not _spans(geometry, grid)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         if fp16_spectra and dtype != torch.float32:
             raise ValueError("fp16_spectra needs dtype torch.float32")
@@ -122,6 +134,12 @@ class PipeSolver:
     def green_spectrum(self):
         import numpy as np
         nx, ny, nz = self.shape
+        if self.general:
+            # four complex tables [cc, cr, rc, rr][kz][ky][kx] on the doubled transverse grid
+            raw = np.empty((4, nz + 1, 2 * ny, 2 * nx, 2), dtype=np.float64)
+            check(self.lib.pipe_green_spectrum(self.handle, raw.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                               raw.size), "pipe_green_spectrum")
+            return raw[..., 0] + 1j * raw[..., 1]
         planes = nz + 1 if self.banded is None else self.banded + 1
         out = np.empty((planes, ny + 1, nx + 1), dtype=np.float64)
         check(self.lib.pipe_green_spectrum(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),

@@ -72,8 +72,10 @@ size_t cplx_size(int dtype) { return dtype == PIPE_F64 ? 16 : 8; }
 // allocate everything but the Green spectrum; fill the twiddle tables
 int alloc_common(pipe_handle* h) {
   const pipe_grid& g = h->grid;
-  // Green planes: the 3-D octant, or the n_nb + 1 2-D spectra of the banded form
-  const size_t oct = size_t(g.nx + 1) * (g.ny + 1) * (h->banded >= 0 ? h->banded + 1 : g.nz + 1);
+  // Green planes: the 3-D octant, the n_nb + 1 2-D spectra of the banded form,
+  // or (general meshes) four complex tables [4][nz+1][2ny][2nx]
+  const size_t oct = h->general ? size_t(8) * (g.nz + 1) * (2 * g.ny) * (2 * g.nx)
+                                : size_t(g.nx + 1) * (g.ny + 1) * (h->banded >= 0 ? h->banded + 1 : g.nz + 1);
   const size_t work = size_t(g.nz + 1) * g.nx * g.ny * cplx_size(g.dtype);
   cudaError_t e;
   if ((e = cudaMalloc(&h->green64, oct * sizeof(double))) != cudaSuccess) return status_of(e);
@@ -152,6 +154,7 @@ SolveArgs<double> make_args<double>(pipe_handle* h, const void* rho, void* phi, 
 
 template <typename T>
 cudaError_t transverse_stage(pipe_handle* h, bool adjoint, const SolveArgs<T>& a, cudaStream_t st) {
+  if (h->general) return launch_transverse_gen<T>(adjoint, h->plan.t_threads, a, st);
   if (h->images)
     return launch_transverse_sym<T>(adjoint, h->plan.t_kind, h->plan.t_h, h->plan.t_threads, a, st);
   return launch_transverse<T>(adjoint, h->free_plan.t_h, h->free_plan.t_threads, a, st);
@@ -252,12 +255,17 @@ static int setup_pipe(const pipe_geometry* geom, const pipe_grid* grid, int igf,
   if (geom->y0 + (grid->ny - 1) * grid->hy > geom->b * (1 + tol)) return PIPE_EINVAL;
   if (st != PIPE_OK) return st;
   if (geom->modes_m > 4096 || geom->modes_n > 4096) return PIPE_EUNSUPPORTED;
-  // meshes spanning the pipe with integer correlation shifts
-  if (std::fabs(grid->nx * grid->hx - geom->a) > 1e-12 * geom->a) return PIPE_EUNSUPPORTED;
-  if (std::fabs(grid->ny * grid->hy - geom->b) > 1e-12 * geom->b) return PIPE_EUNSUPPORTED;
+  // meshes spanning the pipe with integer correlation shifts use the real
+  // octant; any other mesh inside the pipe (a transverse window) the four
+  // full tables, for planes up to 64 x 64
   int sx = 0, sy = 0;
-  if (!near_int(2.0 * geom->x0 / grid->hx, &sx) || !near_int(2.0 * geom->y0 / grid->hy, &sy))
-    return PIPE_EUNSUPPORTED;
+  const bool spanning = std::fabs(grid->nx * grid->hx - geom->a) <= 1e-12 * geom->a &&
+                        std::fabs(grid->ny * grid->hy - geom->b) <= 1e-12 * geom->b &&
+                        near_int(2.0 * geom->x0 / grid->hx, &sx) && near_int(2.0 * geom->y0 / grid->hy, &sy);
+  if (!spanning) {
+    if (grid->nx > 64 || n_nb >= 0 || grid->dtype == PIPE_F32_C16) return PIPE_EUNSUPPORTED;
+    sx = sy = -1;
+  }
 
   if (grid->dtype == PIPE_F32_C16 && (sx != 1 || sy != 1 || n_nb >= 0)) return PIPE_EUNSUPPORTED;
   if (n_nb >= 0) {
@@ -279,8 +287,10 @@ static int setup_pipe(const pipe_geometry* geom, const pipe_grid* grid, int igf,
   h->sy = sy;
   h->images = 1;
   h->banded = n_nb;
+  h->general = spanning ? 0 : 1;
   h->plan = default_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64, sx == 1 && sy == 1);
   if (n_nb >= 0) h->plan.t_threads = 256;
+  if (h->general) h->plan.t_threads = grid->dtype == PIPE_F64 ? 128 : 256;
   h->free_plan = default_free_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
   if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
   GreenSpec s;
@@ -294,7 +304,10 @@ static int setup_pipe(const pipe_geometry* geom, const pipe_grid* grid, int igf,
     s.nz = n_nb;
     s.scale = grid->hx * grid->hy * grid->hz / (4.0 * grid->nx * grid->ny);
   }
-  cudaError_t e = build_pipe_spectrum(s, h->green64, h->green32, nullptr, n_nb < 0);
+  cudaError_t e = h->general
+      ? build_general_spectra(s, geom->x0, geom->y0, reinterpret_cast<double2*>(h->green64),
+                              reinterpret_cast<float2*>(h->green32), nullptr)
+      : build_pipe_spectrum(s, h->green64, h->green32, nullptr, n_nb < 0);
   if (e != cudaSuccess) { free_handle(h); return status_of(e); }
   return finish_setup(h, out);
 }
@@ -383,7 +396,8 @@ int pipe_poisson_solve_host(pipe_handle* h, const void* rho_host, void* phi_host
 int pipe_green_spectrum(pipe_handle* h, double* out, size_t count) {
   if (!h || !out) return PIPE_EINVAL;
   const int planes = h->banded >= 0 ? h->banded + 1 : h->grid.nz + 1;
-  const size_t oct = size_t(h->grid.nx + 1) * (h->grid.ny + 1) * planes;
+  const size_t oct = h->general ? size_t(8) * (h->grid.nz + 1) * (2 * h->grid.ny) * (2 * h->grid.nx)
+                                : size_t(h->grid.nx + 1) * (h->grid.ny + 1) * planes;
   if (count != oct) return PIPE_EINVAL;
   DeviceGuard dg(h->device);
   return status_of(cudaMemcpy(out, h->green64, oct * sizeof(double), cudaMemcpyDeviceToHost));

@@ -293,4 +293,123 @@ done:
   return err;
 }
 
+// ---------------------------------------------------------------------------
+// General meshes (a transverse window, Sec. 5: the mesh need not span the pipe
+// nor sit at integer correlation shifts).  The four tables of Eq. 10 on the
+// doubled grid,
+//     T_xy(p, q, r) = C sum_mn c^x_m(p) c^y_n(q) Z_mn(r),   x, y in {conv, corr},
+// with c^conv_m(p) = cos(m pi o(p) / a), o(p) = p h (p <= n), (p - 2n) h (p > n),
+// c^corr_m(p) = cos(m pi (2 x0 + p h) / a), p = 0..2n-1, and the z profile Z_mn
+// (even in r), are separable per mode, so their forward transforms are
+//     T^_xy(kx, ky, kz) = C sum_m C^x_m(kx) sum_n C^y_n(ky) Z^_mn(kz)
+// with C^ the 2n-point forward DFTs of the cosine factors and Z^ the DCT-I of
+// the z profile.  All FP64; stored [t][kz][ky][kx] complex (t = cc, cr, rc,
+// rr), scaled like the octant.
+// ---------------------------------------------------------------------------
+
+// out[m][k] = sum_p c_m(p) e^{-2 pi i p k / (2n)}, c from offsets (conv or corr)
+__global__ void cos_factor_dft_kernel(double2* out, int M, int n, double h, double a, double origin,
+                                      int corr) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = 2 * n;
+  if (idx >= M * L) return;
+  const int m = idx / L + 1, k = idx % L;
+  double re = 0.0, im = 0.0;
+  for (int p = 0; p < L; ++p) {
+    const double o = corr ? 2.0 * origin + double(p) * h : double(p <= n ? p : p - L) * h;
+    const double c = cospi(double(m) * o / a);
+    double sn, cs;
+    sincospi(2.0 * double((long(p) * k) % L) / double(L), &sn, &cs);
+    re += c * cs;
+    im -= c * sn;
+  }
+  out[idx] = make_double2(re, im);
+}
+
+// Zh[mn][kz] = Z(0) + (-1)^kz Z(nz) + 2 sum_{r=1}^{nz-1} Z(r) cos(pi r kz / nz)
+__global__ void z_dct_kernel(double* Zh, const double* Z, int MN, int nz, const double* cosn) {
+  const long idx = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= long(MN) * (nz + 1)) return;
+  const int kz = int(idx % (nz + 1));
+  const double* z = Z + (idx / (nz + 1)) * (nz + 1);
+  double acc = z[0] + ((kz & 1) ? -z[nz] : z[nz]);
+  for (int r = 1; r < nz; ++r) acc += 2.0 * z[r] * cosn[(long(r) * kz) % (2 * nz)];
+  Zh[idx] = acc;
+}
+
+// W[m][ky][kz] = sum_n Cy[n][ky] Zh[m][n][kz]
+__global__ void general_contract_n_kernel(double2* W, const double2* Cy, const double* Zh, int M, int N,
+                                          int L, int nz) {
+  const long idx = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= long(M) * L * (nz + 1)) return;
+  const int kz = int(idx % (nz + 1));
+  const int ky = int((idx / (nz + 1)) % L);
+  const int m = int(idx / (long(nz + 1) * L));
+  double re = 0.0, im = 0.0;
+  for (int n = 0; n < N; ++n) {
+    const double2 c = Cy[n * L + ky];
+    const double z = Zh[(long(m) * N + n) * (nz + 1) + kz];
+    re += c.x * z;
+    im += c.y * z;
+  }
+  W[idx] = make_double2(re, im);
+}
+
+// T[kz][ky][kx] = C sum_m Cx[m][kx] W[m][ky][kz]  (complex product), FP64 and FP32 copies
+__global__ void general_contract_m_kernel(double2* T64, float2* T32, const double2* Cx, const double2* W, int M,
+                                          int Lx, int Ly, int nz, double C) {
+  const long idx = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= long(nz + 1) * Ly * Lx) return;
+  const int kx = int(idx % Lx);
+  const int ky = int((idx / Lx) % Ly);
+  const int kz = int(idx / (long(Lx) * Ly));
+  double re = 0.0, im = 0.0;
+  for (int m = 0; m < M; ++m) {
+    const double2 c = Cx[m * Lx + kx];
+    const double2 w = W[(long(m) * Ly + ky) * (nz + 1) + kz];
+    re += c.x * w.x - c.y * w.y;
+    im += c.x * w.y + c.y * w.x;
+  }
+  T64[idx] = make_double2(C * re, C * im);
+  T32[idx] = make_float2(float(C * re), float(C * im));
+}
+
+cudaError_t build_general_spectra(const GreenSpec& s, double x0, double y0, double2* t64, float2* t32,
+                                  cudaStream_t st) {
+  const int nx = s.nx, ny = s.ny, nz = s.nz, M = s.modes_m, N = s.modes_n;
+  const int Lx = 2 * nx, Ly = 2 * ny;
+  const long plane = long(nz + 1) * Ly * Lx;
+  double2 *cx[2] = {nullptr, nullptr}, *cy[2] = {nullptr, nullptr}, *W[2] = {nullptr, nullptr};
+  double *Z = nullptr, *Zh = nullptr, *cosn = nullptr;
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < 2; ++k) {
+    if ((err = cudaMalloc(&cx[k], sizeof(double2) * M * Lx)) != cudaSuccess) goto done;
+    if ((err = cudaMalloc(&cy[k], sizeof(double2) * N * Ly)) != cudaSuccess) goto done;
+    if ((err = cudaMalloc(&W[k], sizeof(double2) * size_t(M) * Ly * (nz + 1))) != cudaSuccess) goto done;
+  }
+  if ((err = cudaMalloc(&Z, sizeof(double) * size_t(M) * N * (nz + 1))) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&Zh, sizeof(double) * size_t(M) * N * (nz + 1))) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&cosn, sizeof(double) * 2 * nz)) != cudaSuccess) goto done;
+  for (int k = 0; k < 2; ++k) {                     // k = 0 convolution, 1 correlation
+    cos_factor_dft_kernel<<<nblk(long(M) * Lx, 256), 256, 0, st>>>(cx[k], M, nx, s.hx, s.a, x0, k);
+    cos_factor_dft_kernel<<<nblk(long(N) * Ly, 256), 256, 0, st>>>(cy[k], N, ny, s.hy, s.b, y0, k);
+  }
+  z_profile_kernel<<<nblk(long(M) * N * (nz + 1), 256), 256, 0, st>>>(Z, M, N, nz, s.hz, s.a, s.b, s.igf);
+  cos_pi_table_kernel<<<nblk(2 * nz, 256), 256, 0, st>>>(cosn, nz);
+  z_dct_kernel<<<nblk(long(M) * N * (nz + 1), 256), 256, 0, st>>>(Zh, Z, M * N, nz, cosn);
+  for (int k = 0; k < 2; ++k)
+    general_contract_n_kernel<<<nblk(long(M) * Ly * (nz + 1), 256), 256, 0, st>>>(W[k], cy[k], Zh, M, N, Ly, nz);
+  // t = 2 * (x kind) + (y kind): cc, cr, rc, rr
+  for (int t = 0; t < 4; ++t)
+    general_contract_m_kernel<<<nblk(plane, 256), 256, 0, st>>>(t64 + t * plane, t32 + t * plane, cx[t >> 1],
+                                                                W[t & 1], M, Lx, Ly, nz,
+                                                                2.0 * M_PI / (s.a * s.b) * s.scale);
+  if ((err = cudaGetLastError()) != cudaSuccess) goto done;
+  err = cudaStreamSynchronize(st);
+done:
+  for (int k = 0; k < 2; ++k) { cudaFree(cx[k]); cudaFree(cy[k]); cudaFree(W[k]); }
+  cudaFree(Z); cudaFree(Zh); cudaFree(cosn);
+  return err;
+}
+
 }  // namespace pp

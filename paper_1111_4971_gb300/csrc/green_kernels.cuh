@@ -25,6 +25,12 @@ void launch_tables(V* tw, V* w2, int L, int G, int n2, cudaStream_t st);
 cudaError_t build_pipe_spectrum(const GreenSpec& s, double* g64, float* g32, cudaStream_t st,
                                 bool transform_z = true);
 
+// The four transformed tables of Eq. 10 for a general (window) mesh with
+// origin (x0, y0): FP64 and FP32 copies of [4][nz+1][2ny][2nx] complex values
+// (cc, cr, rc, rr), scaled by s.scale.  Synchronous on `st`.
+cudaError_t build_general_spectra(const GreenSpec& s, double x0, double y0, double2* t64, float2* t32,
+                                  cudaStream_t st);
+
 // Same for the free-space 1/r table (Hockney).
 cudaError_t build_free_spectrum(const GreenSpec& s, double self_value, double* g64, float* g32,
                                 cudaStream_t st);

@@ -24,6 +24,7 @@ struct pipe_handle {
   pipe_grid grid{};
   int kind = 0;          // 0 ordinary, 1 IGF, 2 free space
   int banded = -1;       // >= 0: the banded reduction with this many neighbour planes
+  int general = 0;       // 1: window mesh, the four full transformed tables of Eq. 10
   int sx = 0, sy = 0;    // correlation shifts 2*x0/hx, 2*y0/hy
   int images = 1;        // four-term pipe operator (1) or free space (0)
   double* green64 = nullptr;

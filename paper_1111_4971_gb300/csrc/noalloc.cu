@@ -93,7 +93,7 @@ int noalloc_run(pipe_handle* h, const void* rho, void* phi, void* work, cudaStre
 extern "C" int pipe_poisson_solve_noalloc(pipe_handle* h, const void* rho, void* phi, void* stream) {
   if (!h || !rho || !phi) return PIPE_EINVAL;
   if ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(phi)) % 16) return PIPE_EINVAL;
-  if (h->banded >= 0 || h->grid.dtype == PIPE_F32_C16) return PIPE_EUNSUPPORTED;
+  if (h->banded >= 0 || h->general || h->grid.dtype == PIPE_F32_C16) return PIPE_EUNSUPPORTED;
   const size_t cbytes = h->grid.dtype == PIPE_F64 ? 16 : 8;
   const size_t need = size_t(h->grid.nz + 1) * h->grid.nx * h->grid.ny * cbytes;
   if (need > kNoAllocScratchBytes) return PIPE_EUNSUPPORTED;     // larger than the fixed array

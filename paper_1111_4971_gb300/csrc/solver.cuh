@@ -119,6 +119,9 @@ cudaError_t launch_transverse(bool adjoint, int h, int threads, const SolveArgs<
 cudaError_t launch_z_c16(bool forward, int warps, bool conj, const SolveArgs<float>& a, cudaStream_t st);
 cudaError_t launch_transverse_c16(bool adjoint, int threads, const SolveArgs<float>& a, cudaStream_t st);
 int z_tile_cols(int nz, int warps);
+// transverse stage for general (window) meshes: the four full tables of Eq. 10
+template <typename T>
+cudaError_t launch_transverse_gen(bool adjoint, int threads, const SolveArgs<T>& a, cudaStream_t st);
 // banded z reduction (Eq. 17-18): two kernels on `work` as [nz/2][ny][nx]
 template <typename T>
 cudaError_t launch_banded(int threads, const SolveArgs<T>& a, int n_nb, cudaStream_t st);

@@ -164,7 +164,12 @@ int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
       }, st, reps);
       if (ms > 0 && ms < bz) { bz = ms; best.z_warps = zw; best.z_pipe = zp; }
     }
-  if (h->images) {
+  if (h->general) {                     // window meshes: the general routine's CTA size
+    for (int th : {128, 256, 512}) {
+      float ms = time_ms([&] { return launch_transverse_gen<T>(false, th, a, st); }, st, reps);
+      if (ms > 0 && ms < bt) { bt = ms; best.t_threads = th; }
+    }
+  } else if (h->images) {
     // {kind, CTAs per plane, threads}; kind 1 only for cell-centred meshes
     const int shapes[10][3] = {{0, 1, 128}, {0, 1, 256}, {0, 1, 512}, {0, 2, 128}, {0, 2, 256},
                                {0, 4, 128}, {0, 4, 256}, {1, 1, 128}, {1, 1, 256}, {1, 1, 512}};
@@ -199,7 +204,8 @@ extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
   if (h->grid.dtype == PIPE_F32_C16) return PIPE_OK;     // fixed variant: nothing to choose
   // banded handles are keyed by their neighbour count as well
   const Key k(h->grid.nx, h->grid.nz,
-              h->grid.dtype + (h->images ? 0 : 2) + (h->banded >= 0 ? 4 * (h->banded + 1) : 0));
+              h->grid.dtype + (h->images ? 0 : 3) + (h->general ? 6 : 0) +
+                  (h->banded >= 0 ? 9 * (h->banded + 1) : 0));
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_file_cache();

@@ -74,8 +74,8 @@ def test_setup_validation_without_gpu(L):
         (good_geo, P(96, 96, 256, 1 / 96, 1 / 96, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),  # not 2^k
         (good_geo, P(128, 64, 256, 1 / 128, 1 / 64, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),  # nx != ny
         (good_geo, P(128, 128, 4096, 1 / 128, 1 / 128, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),
-        (G(2.0, 2.0, 0.5, 0.5, 20, 20), P(16, 16, 32, 0.1, 0.1, 0.1, 0), 1,
-         _lib.PIPE_EUNSUPPORTED),                                         # window, not spanning
+        (G(2.0, 2.0, 0.5, 0.5, 20, 20), P(128, 128, 32, 0.01, 0.01, 0.1, 0), 1,
+         _lib.PIPE_EUNSUPPORTED),                                         # window wider than 64
         (G(1.0, 1.0, 0.3 / 128, 0.5 / 128, 20, 20), good, 1, _lib.PIPE_EUNSUPPORTED),  # 2x0/h
     ]
     for geo, grid, igf, want in cases:
