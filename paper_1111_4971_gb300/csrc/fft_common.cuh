@@ -400,6 +400,31 @@ __device__ __forceinline__ void group_fft(V (&v)[GroupShape<L>::E], V* scratch, 
   }
 }
 
+// group_fft with this lane's twiddles in registers: twr[k1] = tw[k1*G + t]
+template <int L, bool INV, typename V>
+__device__ __forceinline__ void group_fft_r(V (&v)[GroupShape<L>::E], V* scratch,
+                                            const V (&twr)[GroupShape<L>::E], int t) {
+  constexpr int G = GroupShape<L>::G;
+  constexpr int E = GroupShape<L>::E;
+  dft_reg<E, INV>(v);
+#pragma unroll
+  for (int k1 = 1; k1 < E; ++k1) v[k1] = cmulc<INV>(v[k1], twr[k1]);
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < E; ++k1) scratch[k1 * (G + 1) + t] = v[k1];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < E / G; ++j) {
+    V u[G];
+    const int k1 = t + G * j;
+#pragma unroll
+    for (int s = 0; s < G; ++s) u[s] = scratch[k1 * (G + 1) + s];
+    dft_reg<G, INV>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < G; ++k2) v[j + (E / G) * k2] = u[k2];
+  }
+}
+
 // Value of the *mirror* element for every e, for a length-L transform split
 // into its even (P=0) or odd (P=1) outputs.  Element q = t + G*e of the half
 // of parity P is paired with q' = (L - q) mod L (P=0) or L-1-q (P=1).  Returns,

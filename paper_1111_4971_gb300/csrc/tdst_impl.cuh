@@ -138,6 +138,23 @@ struct TDst {
   // another plane reuses the buffers.
   __device__ __forceinline__ void plane(const SolveArgs<T>& a, int kz) {
     V* pl = a.work + size_t(kz) * N * N;
+    V ph[E];                                                   // w^{-q} of this lane's slots
+#pragma unroll
+    for (int e = 0; e < E; ++e) ph[e] = sw2[(SGN * (t + G * e)) & MASK];
+    // the group-FFT twiddles of this lane, in registers when they fit (at
+    // most 256 threads), else read from the table at each transform
+    constexpr bool RTW = THREADS <= 256;
+    V twr[RTW ? E : 1];
+    if constexpr (RTW) {
+#pragma unroll
+      for (int k1 = 0; k1 < E; ++k1) twr[k1] = __ldg(&tw[k1 * G + t]);
+    }
+    auto fft = [&](auto inv, V (&x)[E]) {
+      if constexpr (RTW) group_fft_r<N, decltype(inv)::value>(x, scratch, twr, t);
+      else group_fft<N, decltype(inv)::value>(x, scratch, tw, t);
+    };
+    using Fwd = std::integral_constant<bool, INV1>;
+    using Bwd = std::integral_constant<bool, INV2>;
 
     // pass 1: rows i, along y -> ybuf[ky][i], ky = 1..N
 #pragma unroll 1
@@ -146,7 +163,7 @@ struct TDst {
       V v[E];
       if constexpr (H16) load_row16(a, kz, il, v);
       else load_row(pl, il, v);
-      group_fft<N, INV1>(v, scratch, tw, t);                   // V(q)
+      fft(Fwd{}, v);                   // V(q)
       V m[E];
       mirror_fetch<N>(v, m, t, 0, lane - t);                   // V(N-q)
       if (il < N) {
@@ -154,7 +171,7 @@ struct TDst {
         for (int e = 0; e < E; ++e) {
           const int q = t + G * e;
           if (q == 0) ybuf[tile(N, il)] = mk<V>(v[e].x + v[e].x, v[e].y + v[e].y);
-          else ybuf[tile(q, il)] = cfms(v[e], sw2[(SGN * q) & MASK], m[e]);
+          else ybuf[tile(q, il)] = cfms(v[e], ph[e], m[e]);
         }
       }
     }
@@ -177,7 +194,7 @@ struct TDst {
           u[e] = mk<V>(-x.x, -x.y);
         }
       }
-      group_fft<N, INV1>(u, scratch, tw, t);                   // V(kx)
+      fft(Fwd{}, u);                   // V(kx)
       V m[E];
       mirror_fetch<N>(u, m, t, 0, lane - t);
       const T* grow = a.green + (size_t(kz) * (N + 1) + ky) * (N + 1);
@@ -188,7 +205,7 @@ struct TDst {
           const T g = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
           // slot 0 carries kx = N: U(N) = 2 V(0)
           const V w = (kx == 0) ? mk<V>(u[e].x + u[e].x, u[e].y + u[e].y)
-                                : cfms(u[e], sw2[(SGN * kx) & MASK], m[e]);
+                                : cfms(u[e], ph[e], m[e]);
           u[e] = cscale(w, g);                                 // P(kx)
         }
       } else {
@@ -201,7 +218,7 @@ struct TDst {
           const int kx = t + G * e;
           g[e] = act ? float(__ldg(&grow[kx == 0 ? N : kx])) : 0.f;
           u[e] = (kx == 0) ? mk<V>(u[e].x + u[e].x, u[e].y + u[e].y)
-                           : cfms(u[e], sw2[(SGN * kx) & MASK], m[e]);
+                           : cfms(u[e], ph[e], m[e]);
           mu = fmaxf(mu, fmaxf(fabsf(float(u[e].x)), fabsf(float(u[e].y))));
           mg = fmaxf(mg, fabsf(g[e]));
         }
@@ -221,9 +238,9 @@ struct TDst {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int q = t + G * e;
-        if (q != 0) u[e] = cfma_(u[e], sw2[(SGN * q) & MASK], m[e]);   // V'(q); V'(0) = P(N)
+        if (q != 0) u[e] = cfma_(u[e], ph[e], m[e]);   // V'(q); V'(0) = P(N)
       }
-      group_fft<N, INV2>(u, scratch, tw, t);                   // even samples 2n of the column
+      fft(Bwd{}, u);                   // even samples 2n of the column
       if (act) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -249,10 +266,10 @@ struct TDst {
         } else {
           const V p = ybuf[tile(q, i)];
           const V pm = ybuf[tile(N - q, i)];
-          u[e] = cfma_(p, sw2[(SGN * q) & MASK], pm);
+          u[e] = cfma_(p, ph[e], pm);
         }
       }
-      group_fft<N, INV2>(u, scratch, tw, t);
+      fft(Bwd{}, u);
       if constexpr (H16) {
         float mx = 0.f;
 #pragma unroll
