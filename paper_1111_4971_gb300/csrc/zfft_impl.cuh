@@ -59,6 +59,42 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Warp-uniform phase steps of the z transforms, compile-time constants in
+// constant memory (read through the constant cache, off the L1 data path).
+// The phase of output k = 2(t + G e) + p factors into a per-lane part and a
+// part that depends only on the unrolled index e:
+//     w_{2nz}^k = w_{2nz}^{2t+p} * w_nz^{G e},
+// so each lane reads one table value and takes w_nz^{G e} from here.
+constexpr int kZSteps = 84;                       // sum of E over nz = 32..1024
+constexpr int zstep_offset(int nz) {
+  return nz == 32 ? 0 : nz == 64 ? 4 : nz == 128 ? 12 : nz == 256 ? 20 : nz == 512 ? 36 : 52;
+}
+template <typename T>
+struct ZStepTab {
+  T c[kZSteps];
+  T s[kZSteps];
+};
+template <typename T>
+constexpr ZStepTab<T> make_zsteps() {
+  ZStepTab<T> z{};
+  for (int nz = 32; nz <= 1024; nz *= 2) {
+    const int L = nz / 2;
+    const int G = (L <= 32) ? 4 : (L <= 128 ? 8 : (L <= 512 ? 16 : 32));
+    for (int e = 0; e < L / G; ++e) {
+      z.c[zstep_offset(nz) + e] = T(ccos2pi(long(G) * e, nz));
+      z.s[zstep_offset(nz) + e] = T(-csin2pi(long(G) * e, nz));
+    }
+  }
+  return z;
+}
+static __constant__ ZStepTab<float> c_zsteps_f = make_zsteps<float>();
+static __constant__ ZStepTab<double> c_zsteps_d = make_zsteps<double>();
+template <typename T, int NZ>
+__device__ __forceinline__ C2<T> zstep(int e) {              // w_nz^{G e}
+  if constexpr (sizeof(T) == 8) return mk<C2<T>>(c_zsteps_d.c[zstep_offset(NZ) + e], c_zsteps_d.s[zstep_offset(NZ) + e]);
+  else return mk<C2<T>>(c_zsteps_f.c[zstep_offset(NZ) + e], c_zsteps_f.s[zstep_offset(NZ) + e]);
+}
+
 // one CTA of 32*WARPS threads: columns [tile*COLS, (tile+1)*COLS)
 // H16: the spectrum is stored as complex FP16 with one scale per tile
 // (a.zscale[tile]); the reduction scratch follows Cfg::smem_bytes().
@@ -87,20 +123,21 @@ __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsig
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = valid ? __ldg(&src[t + G * e]) : mk<V>(0, 0);
   if (p) {
+    const V b = __ldg(&a.w2_z[2 * t]);
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(&a.w2_z[2 * (t + G * e)]));  // w_nz^m
+    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], cmul(b, zstep<T, NZ>(e)));   // w_nz^m
   }
   group_fft<L, false>(v, scratch, a.tw_z, t);        // v[e] = Z(2q + p), q = t + G e
   const V z0 = v[0];
   V m[E];
   mirror_fetch<L>(v, m, t, p, lane - t);
+  const V bk = __ldg(&a.w2_z[2 * t + p]);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int k = 2 * (t + G * e) + p;
     const V zc = cconj(m[e]);
     const V s = cadd(v[e], zc);
     const V d = csub(v[e], zc);
-    const V wd = cmul(__ldg(&a.w2_z[k]), d);
+    const V wd = cmul(cmul(bk, zstep<T, NZ>(e)), d);           // w_{2nz}^k d, k = 2(t+Ge)+p
     V x = mk<V>(T(0.5) * (s.x + wd.y), T(0.5) * (s.y - wd.x));   // (s - i w d)/2
     v[e] = CONJ ? cconj(x) : x;
   }
@@ -237,19 +274,20 @@ __device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsig
   V m[E];
   mirror_fetch<L>(v, m, t, p, lane - t);
   if (p == 0 && t == 0) m[0] = xN;
+  const V bk = __ldg(&a.w2_z[2 * t + p]);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int k = 2 * (t + G * e) + p;
     const V xm = cconj(m[e]);
     const V s = cadd(v[e], xm);
     const V d = csub(v[e], xm);
-    const V wd = cmulc<true>(d, __ldg(&a.w2_z[k]));           // w_{2nz}^{-k} d
+    const V wd = cmulc<true>(d, cmul(bk, zstep<T, NZ>(e)));   // w_{2nz}^{-k} d, k = 2(t+Ge)+p
     v[e] = mk<V>(s.x - wd.y, s.y + wd.x);                      // s + i w d
   }
   group_fft<L, true>(v, scratch, a.tw_z, t);                  // z_p(m), m = t + G e
   if (p) {
+    const V b = __ldg(&a.w2_z[2 * t]);
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], __ldg(&a.w2_z[2 * (t + G * e)]));
+    for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], cmul(b, zstep<T, NZ>(e)));
   }
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -317,21 +355,23 @@ __device__ __forceinline__ void zfwd_tiles_pipe(const SolveArgs<T>& a, int first
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = src[t + G * e];
     if (p) {
+      const V b = __ldg(&a.w2_z[2 * t]);
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(&a.w2_z[2 * (t + G * e)]));
+      for (int e = 0; e < E; ++e) v[e] = cmul(v[e], cmul(b, zstep<T, NZ>(e)));
     }
     group_fft<L, false>(v, scratch, a.tw_z, t);
     const V z0 = v[0];
     V m[E];
     mirror_fetch<L>(v, m, t, p, lane - t);
     V* mycol = stage + col_local * Cfg::LDS;
+    const V bk = __ldg(&a.w2_z[2 * t + p]);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int kz = 2 * (t + G * e) + p;
       const V zc = cconj(m[e]);
       const V s = cadd(v[e], zc);
       const V d = csub(v[e], zc);
-      const V wd = cmul(__ldg(&a.w2_z[kz]), d);
+      const V wd = cmul(cmul(bk, zstep<T, NZ>(e)), d);
       V x = mk<V>(T(0.5) * (s.x + wd.y), T(0.5) * (s.y - wd.x));
       mycol[kz] = CONJ ? cconj(x) : x;
     }
@@ -407,19 +447,20 @@ __device__ __forceinline__ void zinv_tiles_pipe(const SolveArgs<T>& a, int first
     V m[E];
     mirror_fetch<L>(v, m, t, p, lane - t);
     if (p == 0 && t == 0) m[0] = xN;
+    const V bk = __ldg(&a.w2_z[2 * t + p]);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int kz = 2 * (t + G * e) + p;
       const V xm = cconj(m[e]);
       const V s = cadd(v[e], xm);
       const V d = csub(v[e], xm);
-      const V wd = cmulc<true>(d, __ldg(&a.w2_z[kz]));
+      const V wd = cmulc<true>(d, cmul(bk, zstep<T, NZ>(e)));
       v[e] = mk<V>(s.x - wd.y, s.y + wd.x);
     }
     group_fft<L, true>(v, scratch, a.tw_z, t);
     if (p) {
+      const V b = __ldg(&a.w2_z[2 * t]);
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], __ldg(&a.w2_z[2 * (t + G * e)]));
+      for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], cmul(b, zstep<T, NZ>(e)));
     }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
