@@ -425,6 +425,37 @@ __device__ __forceinline__ void group_fft_r(V (&v)[GroupShape<L>::E], V* scratch
   }
 }
 
+// group_fft whose twiddles w^{t k1} come from a recurrence in k1 restarted
+// from the table every 8 steps (4 table reads per lane instead of E - 1)
+template <int L, bool INV, typename V>
+__device__ __forceinline__ void group_fft_rec(V (&v)[GroupShape<L>::E], V* scratch, const V* __restrict__ tw,
+                                              int t) {
+  constexpr int G = GroupShape<L>::G;
+  constexpr int E = GroupShape<L>::E;
+  dft_reg<E, INV>(v);
+  const V w1 = __ldg(&tw[G + t]);
+  V cur = w1;
+#pragma unroll
+  for (int k1 = 1; k1 < E; ++k1) {
+    if (k1 > 1) cur = ((k1 & 7) == 0) ? __ldg(&tw[k1 * G + t]) : cmul(cur, w1);
+    v[k1] = cmulc<INV>(v[k1], cur);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < E; ++k1) scratch[k1 * (G + 1) + t] = v[k1];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < E / G; ++j) {
+    V u[G];
+    const int k1 = t + G * j;
+#pragma unroll
+    for (int s = 0; s < G; ++s) u[s] = scratch[k1 * (G + 1) + s];
+    dft_reg<G, INV>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < G; ++k2) v[j + (E / G) * k2] = u[k2];
+  }
+}
+
 // Value of the *mirror* element for every e, for a length-L transform split
 // into its even (P=0) or odd (P=1) outputs.  Element q = t + G*e of the half
 // of parity P is paired with q' = (L - q) mod L (P=0) or L-1-q (P=1).  Returns,

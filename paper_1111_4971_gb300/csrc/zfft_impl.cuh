@@ -127,7 +127,7 @@ __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsig
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = cmul(v[e], cmul(b, zstep<T, NZ>(e)));   // w_nz^m
   }
-  group_fft<L, false>(v, scratch, a.tw_z, t);        // v[e] = Z(2q + p), q = t + G e
+  group_fft_rec<L, false>(v, scratch, a.tw_z, t);        // v[e] = Z(2q + p), q = t + G e
   const V z0 = v[0];
   V m[E];
   mirror_fetch<L>(v, m, t, p, lane - t);
@@ -283,7 +283,7 @@ __device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsig
     const V wd = cmulc<true>(d, cmul(bk, zstep<T, NZ>(e)));   // w_{2nz}^{-k} d, k = 2(t+Ge)+p
     v[e] = mk<V>(s.x - wd.y, s.y + wd.x);                      // s + i w d
   }
-  group_fft<L, true>(v, scratch, a.tw_z, t);                  // z_p(m), m = t + G e
+  group_fft_rec<L, true>(v, scratch, a.tw_z, t);                  // z_p(m), m = t + G e
   if (p) {
     const V b = __ldg(&a.w2_z[2 * t]);
 #pragma unroll
@@ -359,7 +359,7 @@ __device__ __forceinline__ void zfwd_tiles_pipe(const SolveArgs<T>& a, int first
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = cmul(v[e], cmul(b, zstep<T, NZ>(e)));
     }
-    group_fft<L, false>(v, scratch, a.tw_z, t);
+    group_fft_rec<L, false>(v, scratch, a.tw_z, t);
     const V z0 = v[0];
     V m[E];
     mirror_fetch<L>(v, m, t, p, lane - t);
@@ -456,7 +456,7 @@ __device__ __forceinline__ void zinv_tiles_pipe(const SolveArgs<T>& a, int first
       const V wd = cmulc<true>(d, cmul(bk, zstep<T, NZ>(e)));
       v[e] = mk<V>(s.x - wd.y, s.y + wd.x);
     }
-    group_fft<L, true>(v, scratch, a.tw_z, t);
+    group_fft_rec<L, true>(v, scratch, a.tw_z, t);
     if (p) {
       const V b = __ldg(&a.w2_z[2 * t]);
 #pragma unroll
