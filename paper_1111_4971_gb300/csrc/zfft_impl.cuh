@@ -95,6 +95,21 @@ __device__ __forceinline__ C2<T> zstep(int e) {              // w_nz^{G e}
   else return mk<C2<T>>(c_zsteps_f.c[zstep_offset(NZ) + e], c_zsteps_f.s[zstep_offset(NZ) + e]);
 }
 
+// FP32: the phase of element (t, e) as (lane base) x (constant step), and the
+// group-FFT twiddles from a short recurrence -- fewer reads through L1, which
+// bounds the FP32 kernels.  FP64 (bound by its arithmetic rate on this GPU):
+// plain table reads, no extra multiplies.
+template <typename T, int NZ>
+__device__ __forceinline__ C2<T> zphase(const C2<T>* __restrict__ w2, C2<T> base, int idx, int e) {
+  if constexpr (sizeof(T) == 4) return cmul(base, zstep<T, NZ>(e));
+  else return __ldg(&w2[idx]);
+}
+template <int L, bool INV, typename V>
+__device__ __forceinline__ void zgroup_fft(V (&v)[GroupShape<L>::E], V* scratch, const V* __restrict__ tw, int t) {
+  if constexpr (sizeof(V) == 8) group_fft_rec<L, INV>(v, scratch, tw, t);
+  else group_fft<L, INV>(v, scratch, tw, t);
+}
+
 // one CTA of 32*WARPS threads: columns [tile*COLS, (tile+1)*COLS)
 // H16: the spectrum is stored as complex FP16 with one scale per tile
 // (a.zscale[tile]); the reduction scratch follows Cfg::smem_bytes().
@@ -125,9 +140,9 @@ __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsig
   if (p) {
     const V b = __ldg(&a.w2_z[2 * t]);
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], cmul(b, zstep<T, NZ>(e)));   // w_nz^m
+    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], zphase<T, NZ>(a.w2_z, b, 2 * (t + G * e), e));   // w_nz^m
   }
-  group_fft_rec<L, false>(v, scratch, a.tw_z, t);        // v[e] = Z(2q + p), q = t + G e
+  zgroup_fft<L, false>(v, scratch, a.tw_z, t);        // v[e] = Z(2q + p), q = t + G e
   const V z0 = v[0];
   V m[E];
   mirror_fetch<L>(v, m, t, p, lane - t);
@@ -137,7 +152,7 @@ __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsig
     const V zc = cconj(m[e]);
     const V s = cadd(v[e], zc);
     const V d = csub(v[e], zc);
-    const V wd = cmul(cmul(bk, zstep<T, NZ>(e)), d);           // w_{2nz}^k d, k = 2(t+Ge)+p
+    const V wd = cmul(zphase<T, NZ>(a.w2_z, bk, 2 * (t + G * e) + p, e), d);           // w_{2nz}^k d, k = 2(t+Ge)+p
     V x = mk<V>(T(0.5) * (s.x + wd.y), T(0.5) * (s.y - wd.x));   // (s - i w d)/2
     v[e] = CONJ ? cconj(x) : x;
   }
@@ -280,14 +295,14 @@ __device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsig
     const V xm = cconj(m[e]);
     const V s = cadd(v[e], xm);
     const V d = csub(v[e], xm);
-    const V wd = cmulc<true>(d, cmul(bk, zstep<T, NZ>(e)));   // w_{2nz}^{-k} d, k = 2(t+Ge)+p
+    const V wd = cmulc<true>(d, zphase<T, NZ>(a.w2_z, bk, 2 * (t + G * e) + p, e));   // w_{2nz}^{-k} d, k = 2(t+Ge)+p
     v[e] = mk<V>(s.x - wd.y, s.y + wd.x);                      // s + i w d
   }
-  group_fft_rec<L, true>(v, scratch, a.tw_z, t);                  // z_p(m), m = t + G e
+  zgroup_fft<L, true>(v, scratch, a.tw_z, t);                  // z_p(m), m = t + G e
   if (p) {
     const V b = __ldg(&a.w2_z[2 * t]);
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], cmul(b, zstep<T, NZ>(e)));
+    for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], zphase<T, NZ>(a.w2_z, b, 2 * (t + G * e), e));
   }
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -357,9 +372,9 @@ __device__ __forceinline__ void zfwd_tiles_pipe(const SolveArgs<T>& a, int first
     if (p) {
       const V b = __ldg(&a.w2_z[2 * t]);
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = cmul(v[e], cmul(b, zstep<T, NZ>(e)));
+      for (int e = 0; e < E; ++e) v[e] = cmul(v[e], zphase<T, NZ>(a.w2_z, b, 2 * (t + G * e), e));
     }
-    group_fft_rec<L, false>(v, scratch, a.tw_z, t);
+    zgroup_fft<L, false>(v, scratch, a.tw_z, t);
     const V z0 = v[0];
     V m[E];
     mirror_fetch<L>(v, m, t, p, lane - t);
@@ -371,7 +386,7 @@ __device__ __forceinline__ void zfwd_tiles_pipe(const SolveArgs<T>& a, int first
       const V zc = cconj(m[e]);
       const V s = cadd(v[e], zc);
       const V d = csub(v[e], zc);
-      const V wd = cmul(cmul(bk, zstep<T, NZ>(e)), d);
+      const V wd = cmul(zphase<T, NZ>(a.w2_z, bk, 2 * (t + G * e) + p, e), d);
       V x = mk<V>(T(0.5) * (s.x + wd.y), T(0.5) * (s.y - wd.x));
       mycol[kz] = CONJ ? cconj(x) : x;
     }
@@ -453,14 +468,14 @@ __device__ __forceinline__ void zinv_tiles_pipe(const SolveArgs<T>& a, int first
       const V xm = cconj(m[e]);
       const V s = cadd(v[e], xm);
       const V d = csub(v[e], xm);
-      const V wd = cmulc<true>(d, cmul(bk, zstep<T, NZ>(e)));
+      const V wd = cmulc<true>(d, zphase<T, NZ>(a.w2_z, bk, 2 * (t + G * e) + p, e));
       v[e] = mk<V>(s.x - wd.y, s.y + wd.x);
     }
-    group_fft_rec<L, true>(v, scratch, a.tw_z, t);
+    zgroup_fft<L, true>(v, scratch, a.tw_z, t);
     if (p) {
       const V b = __ldg(&a.w2_z[2 * t]);
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], cmul(b, zstep<T, NZ>(e)));
+      for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], zphase<T, NZ>(a.w2_z, b, 2 * (t + G * e), e));
     }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
