@@ -135,36 +135,52 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
-    import torch
+def dist_setup(backend="nccl"):
+    """Replica setup from the launcher's environment: one process per GPU
+    (RANK, LOCAL_RANK, WORLD_SIZE, MASTER_ADDR/PORT).  backend "gloo" (CPU)
+    serves the host-side tests of the N > 1 path."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    cuda = backend == "nccl"
+    if cuda:
+        import torch
+        torch.cuda.set_device(local)
     if world > 1:
+        import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(local)
+        if cuda:
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return world, rank, local
 
 
-def barrier(world):
-    import torch
+def barrier(world, cuda=True):
+    """All ranks here, and (on GPUs) this rank's device idle."""
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    torch.cuda.synchronize()
+    if cuda:
+        import torch
+        torch.cuda.synchronize()
 
 
-def max_over_ranks(world, value):
-    import torch
+def max_over_ranks(world, value, device="cuda"):
+    """The slowest rank's value (the job's wall time is set by it)."""
     if world == 1:
         return value
+    import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(world, steps_per_rank, max_total_ms):
+    """Units of all ranks per second: replicas each run `steps_per_rank` solves,
+    the job takes the slowest rank's time."""
+    return world * steps_per_rank / (max_total_ms / 1e3)
 
 
 def cpu_oracle_baseline(w, steps=1):
@@ -376,7 +392,7 @@ def run_ours(args):
     }
     total_ms = max_over_ranks(world, sum(solve_ms))
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(world, args.steps, total_ms)
 
     # ---- end to end through host buffers (copies inside the call) ---------
     rho_h = torch.tensor(rho_np, dtype=torch.float32).pin_memory()
@@ -392,7 +408,7 @@ def run_ours(args):
         s32.solve_host(rho_h, phi_h)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_total = max_over_ranks(world, sum(e2e_ms))
-    e2e_value = world * args.steps / (e2e_total / 1e3)
+    e2e_value = whole_job_rate(world, args.steps, e2e_total)
     nbytes = nx * ny * nz * 4
 
     # ---- roofline of the dominant kernel ---------------------------------
