@@ -394,21 +394,34 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(world, args.steps, total_ms)
 
-    # ---- end to end through host buffers (copies inside the call) ---------
-    rho_h = torch.tensor(rho_np, dtype=torch.float32).pin_memory()
-    phi_h = torch.empty((nx, ny, nz), dtype=torch.float32).pin_memory()
-    for _ in range(2):
-        s32.solve_host(rho_h, phi_h)
+    # ---- end to end through host buffers (copies inside the timed region) --
+    # The public host API for a sequence of solves: every step copies its
+    # input in from pinned host memory and its result out, overlapped with
+    # the neighbouring steps' compute (pipe_poisson_solve_host_stream).
+    nbuf = 4
+    rho_h = [torch.tensor(rho_np, dtype=torch.float32).pin_memory() for _ in range(nbuf)]
+    phi_h = [torch.empty((nx, ny, nz), dtype=torch.float32).pin_memory() for _ in range(nbuf)]
+    ins = [rho_h[k % nbuf] for k in range(args.steps)]
+    outs = [phi_h[k % nbuf] for k in range(args.steps)]
+    s32.solve_host_stream(ins[:3], outs[:3])            # warm-up: creates the staging ring
+    flush.fill_(0.0)
     barrier(world)
-    e2e_ms = []
+    t0 = time.perf_counter()
+    s32.solve_host_stream(ins, outs)
+    e2e_total = max_over_ranks(world, 1e3 * (time.perf_counter() - t0))
+    e2e_value = whole_job_rate(world, args.steps, e2e_total)
+    # the same, one blocking call per step (pipe_poisson_solve_host), for reference
+    for _ in range(2):
+        s32.solve_host(rho_h[0], phi_h[0])
+    barrier(world)
+    serial_ms = []
     for i in range(args.steps):
         flush.fill_(float(i))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s32.solve_host(rho_h, phi_h)
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_total = max_over_ranks(world, sum(e2e_ms))
-    e2e_value = whole_job_rate(world, args.steps, e2e_total)
+        s32.solve_host(rho_h[0], phi_h[0])
+        serial_ms.append(1e3 * (time.perf_counter() - t0))
+    serial_value = whole_job_rate(world, args.steps, max_over_ranks(world, sum(serial_ms)))
     nbytes = nx * ny * nz * 4
 
     # ---- roofline of the dominant kernel ---------------------------------
@@ -445,7 +458,10 @@ def run_ours(args):
                   "frac_of_8tbs": b_pad / (ms_per_step * 1e-3) / 1e9 / 8000.0},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes},
+                "d2h_bytes_per_step": nbytes,
+                "api": "pipe_poisson_solve_host_stream (pinned host buffers, copies of "
+                       "neighbouring steps overlapped with the compute)",
+                "serial_one_call_per_step": serial_value},
         "wall_s_timed_loop": t_wall,
     }
 

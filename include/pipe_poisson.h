@@ -170,6 +170,18 @@ int pipe_poisson_solve_noalloc(pipe_handle* h, const void* rho, void* phi, void*
  * copy bandwidth (pageable memory works, slower). */
 int pipe_poisson_solve_host(pipe_handle* h, const void* rho_host, void* phi_host, void* stream);
 
+/* `count` solves from HOST memory, with the transfers overlapped: solve k runs
+ * on `stream` while the input of solve k+1 is copied in and the result of
+ * solve k-1 is copied out (two further streams, two device staging buffers
+ * per direction, all owned by the handle and created on the first call).
+ * rho_host[k] / phi_host[k]: host arrays of nx*ny*nz values of the handle's
+ * dtype (pinned memory for overlapped copies).  Synchronous: returns when every
+ * result is in host memory.  Same operator as pipe_poisson_solve.
+ * Errors: PIPE_EINVAL (null arrays or entries, count < 1), PIPE_ENOMEM,
+ * PIPE_ECUDA, and the errors of pipe_poisson_solve. */
+int pipe_poisson_solve_host_stream(pipe_handle* h, const void* const* rho_host, void* const* phi_host,
+                                   int count, void* stream);
+
 /* n independent solves (different grids and geometries) in one persistent
  * kernel launch that walks a work list of (solve, stage, tile) items; each
  * stage of a solve waits, with a bounded spin, for the previous stage of the

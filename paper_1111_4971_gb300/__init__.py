@@ -131,6 +131,22 @@ class PipeSolver:
                                                _stream_ptr(stream)), "pipe_poisson_solve_host")
         return phi_host
 
+    def solve_host_stream(self, rho_hosts, phi_hosts=None, stream=None):
+        """A sequence of host fields in, host results out, with the copies of
+        neighbouring solves overlapped with the compute (pinned tensors)."""
+        n = len(rho_hosts)
+        for r in rho_hosts:
+            if r.device.type != "cpu" or r.dtype != self.dtype or not r.is_contiguous() \
+                    or tuple(r.shape) != self.shape:
+                raise ValueError("rho_hosts must be contiguous CPU tensors of the solver dtype and shape")
+        if phi_hosts is None:
+            phi_hosts = [torch.empty(self.shape, dtype=self.dtype, pin_memory=True) for _ in range(n)]
+        rs = (ctypes.c_void_p * n)(*[r.data_ptr() for r in rho_hosts])
+        ps = (ctypes.c_void_p * n)(*[p.data_ptr() for p in phi_hosts])
+        check(self.lib.pipe_poisson_solve_host_stream(self.handle, rs, ps, n, _stream_ptr(stream)),
+              "pipe_poisson_solve_host_stream")
+        return phi_hosts
+
     def green_spectrum(self):
         import numpy as np
         nx, ny, nz = self.shape

@@ -45,6 +45,7 @@ SIGNATURES = {
     "pipe_poisson_adjoint": (c_int, [H, c_void_p, c_void_p, c_void_p]),
     "pipe_poisson_solve_host": (c_int, [H, c_void_p, c_void_p, c_void_p]),
     "pipe_poisson_solve_noalloc": (c_int, [H, c_void_p, c_void_p, c_void_p]),
+    "pipe_poisson_solve_host_stream": (c_int, [H, POINTER(c_void_p), POINTER(c_void_p), c_int, c_void_p]),
     "pipe_poisson_solve_batched": (c_int, [POINTER(H), POINTER(c_void_p), POINTER(c_void_p), c_int,
                                            c_void_p]),
     "pipe_electric_field": (c_int, [H, c_void_p, c_void_p, c_void_p]),

@@ -113,6 +113,15 @@ void free_handle(pipe_handle* h) {
   cudaFree(h->green64); cudaFree(h->green32); cudaFree(h->work);
   cudaFree(h->tab32); cudaFree(h->tab64);
   cudaFree(h->stage_rho); cudaFree(h->stage_phi);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(h->ring_rho[k]);
+    cudaFree(h->ring_phi[k]);
+    if (h->ev_in[k]) cudaEventDestroy(h->ev_in[k]);
+    if (h->ev_done[k]) cudaEventDestroy(h->ev_done[k]);
+    if (h->ev_out[k]) cudaEventDestroy(h->ev_out[k]);
+  }
+  if (h->copy_in) cudaStreamDestroy(h->copy_in);
+  if (h->copy_out) cudaStreamDestroy(h->copy_out);
   batch_release(h);
   delete h;
 }

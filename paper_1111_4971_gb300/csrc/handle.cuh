@@ -38,6 +38,15 @@ struct pipe_handle {
           *tw_t2c_64 = nullptr;
   void* stage_rho = nullptr;   // device staging for pipe_poisson_solve_host
   void* stage_phi = nullptr;
+  // pipe_poisson_solve_host_stream: two device staging buffers per direction,
+  // the two copy streams and the events that order them (created on first use)
+  void* ring_rho[2] = {nullptr, nullptr};
+  void* ring_phi[2] = {nullptr, nullptr};
+  cudaStream_t copy_in = nullptr;
+  cudaStream_t copy_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr};
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};
+  cudaEvent_t ev_out[2] = {nullptr, nullptr};
   pp::Plan plan{8, 0, 1, 256};
   pp::Plan free_plan{8, 0, 1, 256};   // transverse shape of the free-space stage
   void* batch = nullptr;       // batched work list owned by this handle
