@@ -268,8 +268,9 @@ int pipe_autotune(pipe_handle* h, void* stream);
  * nx/t_h rows), t_threads in {128, 256, 512}, t_kind in {0, 1}: 0 computes
  * each transverse line with the padded 2n-point transforms of Eq. 10 (any
  * supported mesh); 1 computes the same combinations with n-point transforms,
- * for cell-centred meshes only (2*x0/hx == 2*y0/hy == 1), t_h == 1 and an
- * nx*ny complex plane of at most 200 KB (FP32 up to 128^2, FP64 up to 64^2).
+ * for cell-centred meshes only (2*x0/hx == 2*y0/hy == 1) and t_h == 1; its
+ * plane buffer is in shared memory, or for FP64 128^2 planes in global
+ * scratch planes that the setup allocates ((nz+1)*nx*ny complex).
  * pipe_set_plan returns PIPE_EINVAL for values outside those sets and
  * PIPE_EUNSUPPORTED for t_kind 1 on other meshes; a variant that does not fit
  * the device (shared memory) makes the next solve fail with PIPE_ECUDA.

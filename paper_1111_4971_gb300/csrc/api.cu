@@ -113,6 +113,7 @@ void free_handle(pipe_handle* h) {
   cudaFree(h->green64); cudaFree(h->green32); cudaFree(h->work);
   cudaFree(h->tab32); cudaFree(h->tab64);
   cudaFree(h->stage_rho); cudaFree(h->stage_phi);
+  cudaFree(h->tbuf);
   for (int k = 0; k < 2; ++k) {
     cudaFree(h->ring_rho[k]);
     cudaFree(h->ring_phi[k]);
@@ -158,6 +159,7 @@ SolveArgs<double> make_args<double>(pipe_handle* h, const void* rho, void* phi, 
   a.tw_t2c = h->tw_t2c_64;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  a.tbuf = static_cast<double2*>(h->tbuf);
   return a;
 }
 
@@ -302,6 +304,12 @@ static int setup_pipe(const pipe_geometry* geom, const pipe_grid* grid, int igf,
   if (h->general) h->plan.t_threads = grid->dtype == PIPE_F64 ? 128 : 256;
   h->free_plan = default_free_plan(grid->nx, grid->nz, grid->dtype == PIPE_F64);
   if ((st = alloc_common(h)) != PIPE_OK) { free_handle(h); return st; }
+  // FP64 planes too large for shared memory: the n-point routine's plane
+  // buffers in global memory (one per kz plane)
+  if (!h->general && n_nb < 0 && sx == 1 && sy == 1 && cplx_size(grid->dtype) * grid->nx * grid->ny > 200 * 1024) {
+    const size_t tb = size_t(grid->nz + 1) * grid->nx * grid->ny * cplx_size(grid->dtype);
+    if (cudaMalloc(&h->tbuf, tb) != cudaSuccess) { free_handle(h); return PIPE_ENOMEM; }
+  }
   GreenSpec s;
   s.nx = grid->nx; s.ny = grid->ny; s.nz = grid->nz;
   s.hx = grid->hx; s.hy = grid->hy; s.hz = grid->hz;

@@ -305,6 +305,7 @@ SolveArgs<double> batch_args<double>(pipe_handle* h) {
   a.work = static_cast<double2*>(h->work); a.green = h->green64;
   a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64; a.tw_t2 = h->tw_t2_64;
   a.tw_t2c = h->tw_t2c_64;
+  a.tbuf = static_cast<double2*>(h->tbuf);
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;

@@ -32,6 +32,9 @@ struct SolveArgs {
   float* zscale;
   float* tscale;
   int zcols;
+  // global scratch planes [nz+1][nx][ny] for the n-point routine when a plane
+  // does not fit in shared memory (FP64 at 128 x 128); null otherwise
+  C2<T>* tbuf;
 };
 
 // z transforms: one CTA handles COLS consecutive (i,j) columns.

@@ -35,7 +35,9 @@
 
 namespace pp {
 
-template <typename T, int N, int THREADS>
+// GB: the plane buffer in a global scratch plane (a.tbuf, L2-resident)
+// instead of shared memory, for planes too large for it (FP64 128 x 128)
+template <typename T, int N, int THREADS, bool GB = false>
 struct TDstCfg {
   using S = GroupShape<N>;
   static constexpr int G = S::G;
@@ -45,7 +47,7 @@ struct TDstCfg {
   static constexpr int YBUF = N * LD;
   static constexpr int GROUPS = THREADS / G;
   static constexpr size_t smem_bytes() {
-    return sizeof(C2<T>) * (size_t(YBUF) + size_t(2 * N) + size_t(GROUPS) * S::SSTRIDE);
+    return sizeof(C2<T>) * ((GB ? 0 : size_t(YBUF)) + size_t(2 * N) + size_t(GROUPS) * S::SSTRIDE);
   }
 };
 
@@ -59,9 +61,9 @@ __device__ __forceinline__ V cfma_(V a, V w, V b) {
 // with the z-forward tile scales, the Green product is taken in FP16 with one
 // scale per column for each operand, and the result is stored as __half2
 // with one scale per row (a.tscale).
-template <typename T, int N, int THREADS, bool ADJ, bool H16 = false>
+template <typename T, int N, int THREADS, bool ADJ, bool H16 = false, bool GB = false>
 struct TDst {
-  using Cfg = TDstCfg<T, N, THREADS>;
+  using Cfg = TDstCfg<T, N, THREADS, GB>;
   using V = C2<T>;
   static constexpr int G = Cfg::G, E = Cfg::E, H = E / 2;
   static constexpr int WARPS = THREADS / 32;
@@ -78,8 +80,8 @@ struct TDst {
   int lane, t, line;
 
   __device__ __forceinline__ TDst(const SolveArgs<T>& a, unsigned char* smem_raw) {
-    ybuf = reinterpret_cast<V*>(smem_raw);
-    sw2 = ybuf + Cfg::YBUF;
+    ybuf = reinterpret_cast<V*>(smem_raw);           // (GB: set per plane)
+    sw2 = GB ? ybuf : ybuf + Cfg::YBUF;
     scratch = sw2 + 2 * N + (threadIdx.x / G) * GroupShape<N>::SSTRIDE;
     tw = a.tw_t;
     lane = threadIdx.x & 31;
@@ -138,12 +140,13 @@ struct TDst {
   // another plane reuses the buffers.
   __device__ __forceinline__ void plane(const SolveArgs<T>& a, int kz) {
     V* pl = a.work + size_t(kz) * N * N;
+    if constexpr (GB) ybuf = a.tbuf + size_t(kz) * N * N;
     V ph[E];                                                   // w^{-q} of this lane's slots
 #pragma unroll
     for (int e = 0; e < E; ++e) ph[e] = sw2[(SGN * (t + G * e)) & MASK];
     // the group-FFT twiddles of this lane, in registers when they fit (at
     // most 256 threads), else read from the table at each transform
-    constexpr bool RTW = THREADS <= 256;
+    constexpr bool RTW = THREADS <= 256 && !GB;
     V twr[RTW ? E : 1];
     if constexpr (RTW) {
 #pragma unroll
@@ -300,9 +303,9 @@ struct TDst {
 };
 
 // one plane
-template <typename T, int N, int THREADS, bool ADJ, bool H16 = false>
+template <typename T, int N, int THREADS, bool ADJ, bool H16 = false, bool GB = false>
 __device__ __forceinline__ void tdst_plane(const SolveArgs<T>& a, int kz, unsigned char* smem_raw) {
-  TDst<T, N, THREADS, ADJ, H16> r(a, smem_raw);
+  TDst<T, N, THREADS, ADJ, H16, GB> r(a, smem_raw);
   r.load_tables(a);
   __syncthreads();
   r.plane(a, kz);

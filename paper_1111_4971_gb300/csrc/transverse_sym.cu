@@ -66,20 +66,23 @@ static cudaError_t tclaunch(const SolveArgs<T>& a, cudaStream_t st) {
 }
 
 // the N-point routine for cell-centred meshes: one CTA per kz plane
-template <typename T, int N, int THREADS, bool ADJ, bool H16 = false>
+template <typename T, int N, int THREADS, bool ADJ, bool H16 = false, bool GB = false>
 __global__ void __launch_bounds__(THREADS, 1) transverse_dst_kernel(SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  tdst_plane<T, N, THREADS, ADJ, H16>(a, blockIdx.x, smem_raw);
+  tdst_plane<T, N, THREADS, ADJ, H16, GB>(a, blockIdx.x, smem_raw);
 }
 
+// planes that do not fit in shared memory go through the global scratch a.tbuf
 template <typename T, int N, int THREADS, bool ADJ, bool H16 = false>
 static cudaError_t tdlaunch(const SolveArgs<T>& a, cudaStream_t st) {
-  using Cfg = TDstCfg<T, N, THREADS>;
-  if constexpr (Cfg::smem_bytes() > kMaxSmem) {
+  constexpr bool GB = TDstCfg<T, N, THREADS, false>::smem_bytes() > kMaxSmem;
+  using Cfg = TDstCfg<T, N, THREADS, GB>;
+  if constexpr (Cfg::smem_bytes() > kMaxSmem || (GB && H16)) {
     return cudaErrorInvalidConfiguration;
   } else {
+    if (GB && !a.tbuf) return cudaErrorInvalidConfiguration;
     const size_t smem = Cfg::smem_bytes();
-    void (*kern)(SolveArgs<T>) = transverse_dst_kernel<T, N, THREADS, ADJ, H16>;
+    void (*kern)(SolveArgs<T>) = transverse_dst_kernel<T, N, THREADS, ADJ, H16, GB>;
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;

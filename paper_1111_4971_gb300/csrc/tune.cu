@@ -39,6 +39,9 @@ Plan default_plan(int n, int nz, bool f64, bool cell_centred) {
   } else {
     p.t_h = 2;
     p.t_threads = 128;
+    // FP64 128^2 on cell-centred meshes: the n-point routine with its plane
+    // buffers in global memory (the handle allocates them)
+    if (cell_centred) { p.t_kind = 1; p.t_h = 1; p.t_threads = 256; }
   }
   return p;
 }
@@ -108,6 +111,7 @@ SolveArgs<double> args_for<double>(pipe_handle* h, void* rho, void* phi) {
   a.tw_t = h->tw_t64; a.w2_t = h->w2_t64; a.tw_z = h->tw_z64; a.w2_z = h->w2_z64;
   a.tw_t2 = h->tw_t2_64;
   a.tw_t2c = h->tw_t2c_64;
+  a.tbuf = static_cast<double2*>(h->tbuf);
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   return a;
@@ -254,7 +258,7 @@ extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, i
     // plane, the N x N plane buffer in shared memory
     if (!h->images || h->sx != 1 || h->sy != 1 || t_h != 1) return PIPE_EUNSUPPORTED;
     const size_t c = h->grid.dtype == PIPE_F64 ? 16 : 8;
-    if (c * h->grid.nx * h->grid.ny > 200 * 1024) return PIPE_EUNSUPPORTED;
+    if (c * h->grid.nx * h->grid.ny > 200 * 1024 && !h->tbuf) return PIPE_EUNSUPPORTED;
   }
   if (h->images) h->plan = Plan{z_warps, z_pipe, t_h, t_threads, t_kind};
   else {
