@@ -89,8 +89,13 @@ struct TDst {
     line = lane / G + GPW * (threadIdx.x >> 5);                // groups of a warp: adjacent lines
   }
 
+  // the plane buffer [ky-1][i] with row i XOR-swizzled by a function of ky
+  // whose bit 0 alternates with ky and whose bits 1-3 differ over any 8
+  // consecutive ky: conflict-free (two wavefronts per warp access) for the
+  // row stores, the column loads / stores and both last-pass loads
   __device__ static __forceinline__ int tile(int ky, int il) {
-    return (ky - 1) * Cfg::LD + (il ^ ((ky - 1) & Cfg::SWM));
+    const int x = ky - 1;
+    return x * Cfg::LD + (il ^ (((2 * x) & Cfg::SWM & ~1) | (x & 1)));
   }
 
   // the even/odd-split samples v_n of row il (row 0 stands in past the end)
