@@ -50,9 +50,12 @@ struct ZCfg {
   static constexpr int COLS = WARPS * CPW;         // columns per CTA
   static constexpr int THREADS = 32 * WARPS;
   static constexpr int GROUPS = THREADS / G;
-  // staging tile, column major [COLS][LDS]: a lane's column is contiguous, and
-  // the odd stride spreads a row (fixed kz, consecutive columns) over the banks
-  static constexpr int LDS = NZ + 1;
+  // staging tile, column major [COLS][LDS]: a lane's column is contiguous; the
+  // stride (in complex values) makes the row-wise accesses (fixed kz,
+  // consecutive columns: the 16-byte store reads of the forward kernel and the
+  // asynchronous copies of the inverse) conflict-free: 2 (mod 16) for 8-byte
+  // values served per half-warp, odd for 16-byte values served per quarter-warp
+  static constexpr int LDS = NZ + (sizeof(T) == 4 ? 2 : 1);
   // single-tile routines: the FFT scratch tiles and the staging tile are live
   // at different times and share the allocation
   static constexpr size_t SCR = size_t(GROUPS) * S::SSTRIDE;
