@@ -202,15 +202,21 @@ struct TDst {
           u[e] = mk<V>(-x.x, -x.y);
         }
       }
+      const T* grow = a.green + (size_t(kz) * (N + 1) + ky) * (N + 1);
+      T gpre[E];                       // the Green row, read before the transform
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int kx = t + G * e;
+        gpre[e] = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
+      }
       fft(Fwd{}, u);                   // V(kx)
       V m[E];
       mirror_fetch<N>(u, m, t, 0, lane - t);
-      const T* grow = a.green + (size_t(kz) * (N + 1) + ky) * (N + 1);
       if constexpr (!H16) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int kx = t + G * e;
-          const T g = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
+          const T g = gpre[e];
           // slot 0 carries kx = N: U(N) = 2 V(0)
           const V w = (kx == 0) ? mk<V>(u[e].x + u[e].x, u[e].y + u[e].y)
                                 : cfms(u[e], ph[e], m[e]);
@@ -224,7 +230,7 @@ struct TDst {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int kx = t + G * e;
-          g[e] = act ? float(__ldg(&grow[kx == 0 ? N : kx])) : 0.f;
+          g[e] = float(gpre[e]);
           u[e] = (kx == 0) ? mk<V>(u[e].x + u[e].x, u[e].y + u[e].y)
                            : cfms(u[e], ph[e], m[e]);
           mu = fmaxf(mu, fmaxf(fabsf(float(u[e].x)), fabsf(float(u[e].y))));
