@@ -265,18 +265,30 @@ int pipe_autotune(pipe_handle* h, void* stream);
  * the z transforms), z_pipe in {0, 1} (1: each z CTA walks several tiles and
  * streams the next tile's input while transforming the current one), t_h in
  * {1, 2, 4} (the transverse stage runs t_h CTAs per kz plane, each holding
- * nx/t_h rows), t_threads in {128, 256, 512}, t_kind in {0, 1}: 0 computes
+ * nx/t_h rows), t_threads in {128, 256, 512}, t_kind in {0, 1, 2}: 0 computes
  * each transverse line with the padded 2n-point transforms of Eq. 10 (any
  * supported mesh); 1 computes the same combinations with n-point transforms,
  * for cell-centred meshes only (2*x0/hx == 2*y0/hy == 1) and t_h == 1; its
  * plane buffer is in shared memory, or for FP64 128^2 planes in global
- * scratch planes that the setup allocates ((nz+1)*nx*ny complex).
- * pipe_set_plan returns PIPE_EINVAL for values outside those sets and
- * PIPE_EUNSUPPORTED for t_kind 1 on other meshes; a variant that does not fit
- * the device (shared memory) makes the next solve fail with PIPE_ECUDA.
+ * scratch planes that the setup allocates ((nz+1)*nx*ny complex).  2 is the
+ * same arithmetic as 1 in a persistent launch (one CTA per SM looping over
+ * kz planes) whose input rows arrive by bulk asynchronous copies into shared
+ * memory, the next plane's first rows while the current plane is still being
+ * transformed; same meshes as 1, plane buffer in shared memory only (not
+ * FP64 128^2).  pipe_set_plan returns PIPE_EINVAL for values outside those
+ * sets and PIPE_EUNSUPPORTED for t_kind 1 or 2 on other meshes; a variant
+ * that does not fit the device (shared memory) makes the next solve fail
+ * with PIPE_ECUDA.
  * The free-space (Hockney) handle ignores t_kind. */
 int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h, int* t_threads, int* t_kind);
 int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads, int t_kind);
+
+/* The handle's device-side error word, read and cleared (synchronous: waits
+ * for the device).  PIPE_OK, or PIPE_ETIMEOUT when a bounded wait of the
+ * staged transverse kernel (t_kind 2) for its own asynchronous copies gave up
+ * since the last read; the results of the solves in between are then
+ * undefined.  Errors: PIPE_EINVAL (null handle), PIPE_ECUDA. */
+int pipe_status(pipe_handle* h);
 
 /* Electric field E = -grad phi on the handle's mesh (device arrays of the
  * handle's dtype; FP32 for PIPE_F32_C16): phi [nx][ny][nz], E [3][nx][ny][nz]

@@ -194,6 +194,13 @@ class PipeSolver:
         return {"z_warps": z.value, "z_pipe": zp.value, "t_h": h.value, "t_threads": t.value,
                 "t_kind": k.value}
 
+    def status(self):
+        """The handle's device error word, read and cleared (pipe_status)."""
+        st = self.lib.pipe_status(self.handle)
+        if st not in (_lib.PIPE_OK, _lib.PIPE_ETIMEOUT):
+            check(st, "pipe_status")
+        return st
+
     def set_plan(self, z_warps=8, z_pipe=1, t_h=1, t_threads=256, t_kind=0):
         check(self.lib.pipe_set_plan(self.handle, int(z_warps), int(z_pipe), int(t_h), int(t_threads),
                                      int(t_kind)), "pipe_set_plan")

@@ -61,6 +61,7 @@ SIGNATURES = {
     "pipe_get_plan": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
                               POINTER(c_int)]),
     "pipe_set_plan": (c_int, [H, c_int, c_int, c_int, c_int, c_int]),
+    "pipe_status": (c_int, [H]),
     "pipe_cic_deposit": (c_int, [H, c_void_p, c_int64, c_double, c_void_p, c_void_p]),
     "pipe_cic_gather_grad": (c_int, [H, c_void_p, c_int64, c_double, c_void_p, c_void_p, c_void_p]),
     "pipe_green_destroy": (None, [H]),

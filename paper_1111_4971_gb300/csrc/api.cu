@@ -84,7 +84,10 @@ int alloc_common(pipe_handle* h) {
   const int n = g.nx, Lz = g.nz / 2;
   // float2 and double2 tables: tw_t (n), w2_t (2n), tw_z (nz/2), w2_z (2nz)
   const size_t cnt = size_t(n) + 2 * n + Lz + 2 * g.nz + 2 * n + 2 * n;
-  if ((e = cudaMalloc(&h->tab32, cnt * sizeof(float2))) != cudaSuccess) return status_of(e);
+  // one more float2 after the tables holds the device error word
+  if ((e = cudaMalloc(&h->tab32, (cnt + 1) * sizeof(float2))) != cudaSuccess) return status_of(e);
+  h->err = reinterpret_cast<int*>(h->tab32 + cnt);
+  if ((e = cudaMemset(h->err, 0, sizeof(int))) != cudaSuccess) return status_of(e);
   if ((e = cudaMalloc(&h->tab64, cnt * sizeof(double2))) != cudaSuccess) return status_of(e);
   h->tw_t32 = h->tab32; h->w2_t32 = h->tw_t32 + n; h->tw_z32 = h->w2_t32 + 2 * n; h->w2_z32 = h->tw_z32 + Lz;
   h->tw_t2_32 = h->w2_z32 + 2 * g.nz;
@@ -140,6 +143,7 @@ SolveArgs<float> make_args<float>(pipe_handle* h, const void* rho, void* phi, vo
   a.tw_t2c = h->tw_t2c_32;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  a.err = h->err;
   if (h->grid.dtype == PIPE_F32_C16) {
     // work: (nz+1) nx ny complex-FP16 values, then the two scale tables
     const size_t nodes = size_t(h->grid.nx) * h->grid.ny;
@@ -160,6 +164,7 @@ SolveArgs<double> make_args<double>(pipe_handle* h, const void* rho, void* phi, 
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
   a.tbuf = static_cast<double2*>(h->tbuf);
+  a.err = h->err;
   return a;
 }
 
@@ -408,6 +413,17 @@ int pipe_poisson_solve_host(pipe_handle* h, const void* rho_host, void* phi_host
   if ((e = cudaMemcpyAsync(phi_host, h->stage_phi, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return status_of(e);
   return status_of(cudaStreamSynchronize(st));
+}
+
+int pipe_status(pipe_handle* h) {
+  if (!h || !h->err) return PIPE_EINVAL;
+  DeviceGuard dg(h->device);
+  int word = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&word, h->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
+  if (e != cudaSuccess) return status_of(e);
+  return word;
 }
 
 int pipe_green_spectrum(pipe_handle* h, double* out, size_t count) {

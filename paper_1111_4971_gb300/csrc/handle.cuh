@@ -37,6 +37,7 @@ struct pipe_handle {
   double2 *tw_t64 = nullptr, *w2_t64 = nullptr, *tw_z64 = nullptr, *w2_z64 = nullptr, *tw_t2_64 = nullptr,
           *tw_t2c_64 = nullptr;
   void* tbuf = nullptr;        // n-point scratch planes (FP64 at 128 x 128), see SolveArgs::tbuf
+  int* err = nullptr;          // device error word (in the tab32 allocation), see pipe_status
   void* stage_rho = nullptr;   // device staging for pipe_poisson_solve_host
   void* stage_phi = nullptr;
   // pipe_poisson_solve_host_stream: two device staging buffers per direction,

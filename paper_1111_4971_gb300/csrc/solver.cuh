@@ -35,6 +35,9 @@ struct SolveArgs {
   // global scratch planes [nz+1][nx][ny] for the n-point routine when a plane
   // does not fit in shared memory (FP64 at 128 x 128); null otherwise
   C2<T>* tbuf;
+  // device error word of the handle (PIPE_ETIMEOUT when a bounded wait of the
+  // staged transverse kernel gave up); null: not recorded
+  int* err;
 };
 
 // z transforms: one CTA handles COLS consecutive (i,j) columns.

@@ -30,14 +30,57 @@
 // transforms back and stores it in place, pass 3 transforms the rows back.
 #pragma once
 
+#include "../../include/pipe_poisson.h"
 #include "fft_common.cuh"
 #include "solver.cuh"
 
 namespace pp {
 
+// Bulk asynchronous copies (TMA, global -> shared) completed on an mbarrier.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// order this thread's earlier shared-memory accesses (and, after a barrier,
+// the CTA's) before later asynchronous-proxy writes to shared memory
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// one arrival that also announces `bytes` of copies to complete on `bar`,
+// then the copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// non-blocking test of phase `parity` of `bar` (acquire: the copied bytes are
+// visible to the caller once it returns true)
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// polls of a staged-row wait before it gives up (about 0.2 s with the back-off)
+constexpr long kStageSpinLimit = 1L << 21;
+
 // GB: the plane buffer in a global scratch plane (a.tbuf, L2-resident)
-// instead of shared memory, for planes too large for it (FP64 128 x 128)
-template <typename T, int N, int THREADS, bool GB = false>
+// instead of shared memory, for planes too large for it (FP64 128 x 128).
+// STG: the staged persistent form (one CTA per SM looping over planes); the
+// rows of pass 1 arrive by bulk copies in a staging buffer of SR rows, and
+// the first rows of the CTA's next plane are copied in while the current
+// plane is still in passes 2 and 3.
+template <typename T, int N, int THREADS, bool GB = false, bool STG = false>
 struct TDstCfg {
   using S = GroupShape<N>;
   static constexpr int G = S::G;
@@ -46,9 +89,14 @@ struct TDstCfg {
   static constexpr int SWM = (N < 16 ? N : 16) - 1;
   static constexpr int YBUF = N * LD;
   static constexpr int GROUPS = THREADS / G;
-  static constexpr size_t smem_bytes() {
-    return sizeof(C2<T>) * ((GB ? 0 : size_t(YBUF)) + size_t(2 * N) + size_t(GROUPS) * S::SSTRIDE);
-  }
+  static constexpr int GPC = (THREADS / 32) * (32 / G);        // lines in flight per CTA
+  static constexpr int SR = GPC < N ? GPC : N;                 // staged rows per copy
+  static_assert(N % SR == 0, "staged chunks tile the plane");
+  static constexpr size_t STG_OFF =
+      (sizeof(C2<T>) * ((GB ? 0 : size_t(YBUF)) + size_t(2 * N) + size_t(GROUPS) * S::SSTRIDE) + 15) / 16 * 16;
+  static constexpr size_t STG_BYTES = sizeof(C2<T>) * size_t(SR) * N;
+  static constexpr size_t BAR_OFF = STG_OFF + STG_BYTES;
+  static constexpr size_t smem_bytes() { return STG ? BAR_OFF + 16 : STG_OFF; }
 };
 
 // a + w * b
@@ -61,9 +109,10 @@ __device__ __forceinline__ V cfma_(V a, V w, V b) {
 // with the z-forward tile scales, the Green product is taken in FP16 with one
 // scale per column for each operand, and the result is stored as __half2
 // with one scale per row (a.tscale).
-template <typename T, int N, int THREADS, bool ADJ, bool H16 = false, bool GB = false>
+template <typename T, int N, int THREADS, bool ADJ, bool H16 = false, bool GB = false, bool STG = false>
 struct TDst {
-  using Cfg = TDstCfg<T, N, THREADS, GB>;
+  static_assert(!(STG && (GB || H16)), "staged rows: FP32 / FP64 planes in shared memory");
+  using Cfg = TDstCfg<T, N, THREADS, GB, STG>;
   using V = C2<T>;
   static constexpr int G = Cfg::G, E = Cfg::E, H = E / 2;
   static constexpr int WARPS = THREADS / 32;
@@ -77,6 +126,10 @@ struct TDst {
   V* sw2;                                                      // 2N phases w_{2N}^j
   V* scratch;
   const V* tw;                // N-point twiddles, read by group_fft from global memory
+  V* stg;                     // STG: the staged rows [SR][N]
+  uint64_t* bar;              // STG: completion barrier of the staged copies
+  unsigned sphase = 0;        // STG: parity of the next staged chunk
+  bool sfail = false;         // STG: a wait gave up (PIPE_ETIMEOUT recorded)
   int lane, t, line;
 
   __device__ __forceinline__ TDst(const SolveArgs<T>& a, unsigned char* smem_raw) {
@@ -87,6 +140,32 @@ struct TDst {
     lane = threadIdx.x & 31;
     t = lane % G;
     line = lane / G + GPW * (threadIdx.x >> 5);                // groups of a warp: adjacent lines
+    stg = reinterpret_cast<V*>(smem_raw + Cfg::STG_OFF);
+    bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::BAR_OFF);
+  }
+
+  // STG, one thread: copy rows r0 .. r0+SR-1 of plane kz into the staging
+  // buffer (the caller has synchronised after the buffer's last reads)
+  __device__ __forceinline__ void stage_issue(const SolveArgs<T>& a, int kz, int r0) {
+    fence_async_smem();
+    bulk_load(stg, a.work + (size_t(kz) * N + r0) * N, unsigned(Cfg::STG_BYTES), bar);
+  }
+
+  // STG: wait for the next staged chunk; a wait that gives up records
+  // PIPE_ETIMEOUT and later waits return at once, so the kernel always ends
+  __device__ __forceinline__ void stage_wait(const SolveArgs<T>& a) {
+    if (!sfail) {
+      long polls = 0;
+      while (!mbar_test(bar, sphase)) {
+        if (++polls > kStageSpinLimit) {
+          sfail = true;
+          if (a.err) atomicExch(a.err, PIPE_ETIMEOUT);
+          break;
+        }
+        if (polls > 32) __nanosleep(64);
+      }
+    }
+    sphase ^= 1u;
   }
 
   // the plane buffer [ky-1][i] with row i XOR-swizzled by a function of ky
@@ -100,7 +179,9 @@ struct TDst {
 
   // the even/odd-split samples v_n of row il (row 0 stands in past the end)
   __device__ __forceinline__ void load_row(const V* plane, int il, V (&v)[E]) const {
-    const V* row = plane + size_t(il < N ? il : 0) * N;
+    load_row_at(plane + size_t(il < N ? il : 0) * N, v);
+  }
+  __device__ __forceinline__ void load_row_at(const V* row, V (&v)[E]) const {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int n = t + G * e;
@@ -143,7 +224,9 @@ struct TDst {
   // Plane kz in place (the phase table already loaded and synchronised).
   // Ends with the plane's stores issued; the caller synchronises before
   // another plane reuses the buffers.
-  __device__ __forceinline__ void plane(const SolveArgs<T>& a, int kz) {
+  // STG: next >= 0 is the CTA's next plane, whose first rows are copied in
+  // once this plane's pass 1 has read its last staged rows.
+  __device__ __forceinline__ void plane(const SolveArgs<T>& a, int kz, int next = -1) {
     V* pl = a.work + size_t(kz) * N * N;
     if constexpr (GB) ybuf = a.tbuf + size_t(kz) * N * N;
     V ph[E];                                                   // w^{-q} of this lane's slots
@@ -169,8 +252,19 @@ struct TDst {
     for (int r0 = 0; r0 < N; r0 += GPC) {
       const int il = r0 + line;
       V v[E];
-      if constexpr (H16) load_row16(a, kz, il, v);
-      else load_row(pl, il, v);
+      if constexpr (H16) {
+        load_row16(a, kz, il, v);
+      } else if constexpr (STG) {
+        stage_wait(a);
+        load_row_at(stg + size_t(il < N ? il - r0 : 0) * N, v);
+        __syncthreads();               // every lane has read the staged rows
+        if (threadIdx.x == 0) {
+          if (r0 + GPC < N) stage_issue(a, kz, r0 + GPC);
+          else if (next >= 0) stage_issue(a, next, 0);
+        }
+      } else {
+        load_row(pl, il, v);
+      }
       fft(Fwd{}, v);                   // V(q)
       V m[E];
       mirror_fetch<N>(v, m, t, 0, lane - t);                   // V(N-q)
@@ -320,6 +414,31 @@ __device__ __forceinline__ void tdst_plane(const SolveArgs<T>& a, int kz, unsign
   r.load_tables(a);
   __syncthreads();
   r.plane(a, kz);
+}
+
+// the staged persistent form: CTA b takes planes b, b + gridDim.x, ...
+template <typename T, int N, int THREADS, bool ADJ>
+__device__ __forceinline__ void tdst_persistent(const SolveArgs<T>& a, unsigned char* smem_raw) {
+  TDst<T, N, THREADS, ADJ, false, false, true> r(a, smem_raw);
+  const int first = int(blockIdx.x);
+  if (first > a.nz) return;
+  if (threadIdx.x == 0) {
+    mbar_init(r.bar, 1);
+    r.stage_issue(a, first, 0);
+  }
+  r.load_tables(a);
+  __syncthreads();
+#pragma unroll 1
+  for (int kz = first; kz <= a.nz; kz += int(gridDim.x)) {
+    const int next = kz + int(gridDim.x) <= a.nz ? kz + int(gridDim.x) : -1;
+    r.plane(a, kz, next);
+    __syncthreads();                   // before the next plane reuses the buffers
+  }
+  // after a wait gave up a copy may still be in flight: wait for it (bounded)
+  // so that it does not land after the CTA has left
+  if (threadIdx.x == 0 && r.sfail) {
+    for (long polls = 0; polls < kStageSpinLimit && !mbar_test(r.bar, r.sphase); ++polls) __nanosleep(64);
+  }
 }
 
 }  // namespace pp

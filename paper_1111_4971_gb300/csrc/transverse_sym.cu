@@ -92,6 +92,49 @@ static cudaError_t tdlaunch(const SolveArgs<T>& a, cudaStream_t st) {
   }
 }
 
+// the staged persistent form of the N-point routine: one CTA per SM (as many
+// as fit), each looping over planes with its rows copied in ahead by TMA
+template <typename T, int N, int THREADS, bool ADJ>
+__global__ void __launch_bounds__(THREADS, 1) transverse_dsts_kernel(SolveArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tdst_persistent<T, N, THREADS, ADJ>(a, smem_raw);
+}
+
+template <typename T, int N, int THREADS, bool ADJ>
+static cudaError_t tdslaunch(const SolveArgs<T>& a, cudaStream_t st) {
+  using Cfg = TDstCfg<T, N, THREADS, false, true>;
+  if constexpr (Cfg::smem_bytes() > kMaxSmem) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    const size_t smem = Cfg::smem_bytes();
+    void (*kern)(SolveArgs<T>) = transverse_dsts_kernel<T, N, THREADS, ADJ>;
+    cudaError_t e;
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem)) != cudaSuccess) return e;
+    if (per_sm < 1 || sms < 1) return cudaErrorInvalidConfiguration;
+    const int grid = a.nz + 1 < sms * per_sm ? a.nz + 1 : sms * per_sm;
+    kern<<<grid, THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+}
+
+template <typename T, int N>
+static cudaError_t tdslaunch2(bool adjoint, int hb, int threads, const SolveArgs<T>& a, cudaStream_t st) {
+  if (hb != 1 || a.sx != 1 || a.sy != 1) return cudaErrorInvalidValue;
+  switch (threads) {
+    case 128: return adjoint ? tdslaunch<T, N, 128, true>(a, st) : tdslaunch<T, N, 128, false>(a, st);
+    case 256: return adjoint ? tdslaunch<T, N, 256, true>(a, st) : tdslaunch<T, N, 256, false>(a, st);
+    case 512: return adjoint ? tdslaunch<T, N, 512, true>(a, st) : tdslaunch<T, N, 512, false>(a, st);
+    default: return cudaErrorInvalidConfiguration;
+  }
+}
+
 template <typename T, int N>
 static cudaError_t tdlaunch2(bool adjoint, int hb, int threads, const SolveArgs<T>& a, cudaStream_t st) {
   if (hb != 1 || a.sx != 1 || a.sy != 1) return cudaErrorInvalidValue;
@@ -136,6 +179,15 @@ cudaError_t launch_transverse_sym<PP_TS_TYPE>(bool adjoint, int kind, int hb, in
       case 32: return tdlaunch2<T, 32>(adjoint, hb, threads, a, st);
       case 64: return tdlaunch2<T, 64>(adjoint, hb, threads, a, st);
       case 128: return tdlaunch2<T, 128>(adjoint, hb, threads, a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (kind == 2) {
+    switch (a.nx) {
+      case 16: return tdslaunch2<T, 16>(adjoint, hb, threads, a, st);
+      case 32: return tdslaunch2<T, 32>(adjoint, hb, threads, a, st);
+      case 64: return tdslaunch2<T, 64>(adjoint, hb, threads, a, st);
+      case 128: return tdslaunch2<T, 128>(adjoint, hb, threads, a, st);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -23,14 +23,15 @@ namespace pp {
 Plan default_plan(int n, int nz, bool f64, bool cell_centred) {
   Plan p;
   // timed on GB300: FP32 one CTA per plane, on cell-centred meshes with the
-  // n-point routine (256 threads; 512 at n = 64), else the cyclic 2n-point
-  // routine (512 threads); FP64 2-CTA clusters of 128 threads at n = 128
+  // n-point routine (256 threads; 512 at n = 64; at n = 128 its staged
+  // persistent form), else the cyclic 2n-point routine (512 threads); FP64
+  // 2-CTA clusters of 128 threads at n = 128
   p.z_warps = 8;
   p.z_pipe = 0;
   p.t_kind = 0;
   if (!f64) {
     p.t_h = 1;
-    if (cell_centred) { p.t_kind = 1; p.t_threads = n == 64 ? 512 : 256; }
+    if (cell_centred) { p.t_kind = n == 128 ? 2 : 1; p.t_threads = n == 64 ? 512 : 256; }
     else p.t_threads = 512;
   } else if (n < 128) {
     p.t_h = 1;
@@ -174,11 +175,12 @@ int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
       if (ms > 0 && ms < bt) { bt = ms; best.t_threads = th; }
     }
   } else if (h->images) {
-    // {kind, CTAs per plane, threads}; kind 1 only for cell-centred meshes
-    const int shapes[10][3] = {{0, 1, 128}, {0, 1, 256}, {0, 1, 512}, {0, 2, 128}, {0, 2, 256},
-                               {0, 4, 128}, {0, 4, 256}, {1, 1, 128}, {1, 1, 256}, {1, 1, 512}};
+    // {kind, CTAs per plane, threads}; kinds 1 and 2 only for cell-centred meshes
+    const int shapes[13][3] = {{0, 1, 128}, {0, 1, 256}, {0, 1, 512}, {0, 2, 128}, {0, 2, 256},
+                               {0, 4, 128}, {0, 4, 256}, {1, 1, 128}, {1, 1, 256}, {1, 1, 512},
+                               {2, 1, 128}, {2, 1, 256}, {2, 1, 512}};
     for (auto& sh : shapes) {
-      if (sh[0] == 1 && !(h->sx == 1 && h->sy == 1)) continue;
+      if (sh[0] >= 1 && !(h->sx == 1 && h->sy == 1)) continue;
       float ms = time_ms([&] { return launch_transverse_sym<T>(false, sh[0], sh[1], sh[2], a, st); }, st,
                          reps);
       if (ms > 0 && ms < bt) { bt = ms; best.t_kind = sh[0]; best.t_h = sh[1]; best.t_threads = sh[2]; }
@@ -251,14 +253,15 @@ extern "C" int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h
 extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads, int t_kind) {
   if (!h) return PIPE_EINVAL;
   if ((z_warps != 8 && z_warps != 16) || (z_pipe != 0 && z_pipe != 1) || (t_h != 1 && t_h != 2 && t_h != 4) ||
-      (t_threads != 128 && t_threads != 256 && t_threads != 512) || (t_kind != 0 && t_kind != 1))
+      (t_threads != 128 && t_threads != 256 && t_threads != 512) || t_kind < 0 || t_kind > 2)
     return PIPE_EINVAL;
-  if (t_kind == 1) {
+  if (t_kind >= 1) {
     // the N-point routine: pipe operator on cell-centred meshes, one CTA per
-    // plane, the N x N plane buffer in shared memory
+    // plane, the N x N plane buffer in shared memory (kind 1: or in global
+    // scratch planes where the setup allocated them)
     if (!h->images || h->sx != 1 || h->sy != 1 || t_h != 1) return PIPE_EUNSUPPORTED;
     const size_t c = h->grid.dtype == PIPE_F64 ? 16 : 8;
-    if (c * h->grid.nx * h->grid.ny > 200 * 1024 && !h->tbuf) return PIPE_EUNSUPPORTED;
+    if (c * h->grid.nx * h->grid.ny > 200 * 1024 && (t_kind == 2 || !h->tbuf)) return PIPE_EUNSUPPORTED;
   }
   if (h->images) h->plan = Plan{z_warps, z_pipe, t_h, t_threads, t_kind};
   else {
