@@ -4,9 +4,29 @@
 
 namespace pp {
 
+// The tile that a CTA of the next wave will take: this tile plus the number
+// of CTAs resident at once (SMs x CTAs per SM), blocks being issued in order.
+template <int WARPS>
+__device__ __forceinline__ int next_wave_tile() {
+  unsigned nsm;
+  asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+  return int(blockIdx.x) + int(nsm) * (WARPS <= 8 ? 2 : 1);
+}
+
 template <typename T, int NZ, int WARPS, bool CONJ, bool H16>
 __global__ void __launch_bounds__(32 * WARPS, (WARPS <= 8 ? 2 : 1)) zfwd_kernel(SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (threadIdx.x == 0) {
+    // its input columns (contiguous, whole 16-byte units) into L2
+    using Cfg = ZCfg<T, NZ, WARPS>;
+    const int ncols = a.nx * a.ny, c0 = next_wave_tile<WARPS>() * Cfg::COLS;
+    if (c0 < ncols) {
+      const int c1 = c0 + Cfg::COLS < ncols ? c0 + Cfg::COLS : ncols;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a.rho + size_t(c0) * NZ),
+                   "r"(unsigned(sizeof(T) * size_t(c1 - c0) * NZ))
+                   : "memory");
+    }
+  }
   zfwd_tile<T, NZ, WARPS, CONJ, H16>(a, blockIdx.x, smem_raw);
 }
 
