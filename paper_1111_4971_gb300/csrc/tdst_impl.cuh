@@ -128,6 +128,11 @@ struct TDst {
   const V* tw;                // N-point twiddles, read by group_fft from global memory
   V* stg;                     // STG: the staged rows [SR][N]
   uint64_t* bar;              // STG: completion barrier of the staged copies
+  // this lane's per-slot phases w^{-q} and, when they fit in registers (at
+  // most 256 threads, plane buffer in shared memory), its group-FFT twiddles
+  static constexpr bool RTW = THREADS <= 256 && !GB;
+  V ph[E];
+  V twr[RTW ? E : 1];
   unsigned sphase = 0;        // STG: parity of the next staged chunk
   bool sfail = false;         // STG: a wait gave up (PIPE_ETIMEOUT recorded)
   int lane, t, line;
@@ -221,6 +226,17 @@ struct TDst {
     for (int i = threadIdx.x; i < 2 * N; i += THREADS) sw2[i] = a.w2_t[i];
   }
 
+  // this lane's phases and twiddles (after load_tables and a barrier); they
+  // serve every plane the CTA transforms
+  __device__ __forceinline__ void lane_tables() {
+#pragma unroll
+    for (int e = 0; e < E; ++e) ph[e] = sw2[(SGN * (t + G * e)) & MASK];
+    if constexpr (RTW) {
+#pragma unroll
+      for (int k1 = 0; k1 < E; ++k1) twr[k1] = __ldg(&tw[k1 * G + t]);
+    }
+  }
+
   // Plane kz in place (the phase table already loaded and synchronised).
   // Ends with the plane's stores issued; the caller synchronises before
   // another plane reuses the buffers.
@@ -229,17 +245,8 @@ struct TDst {
   __device__ __forceinline__ void plane(const SolveArgs<T>& a, int kz, int next = -1) {
     V* pl = a.work + size_t(kz) * N * N;
     if constexpr (GB) ybuf = a.tbuf + size_t(kz) * N * N;
-    V ph[E];                                                   // w^{-q} of this lane's slots
-#pragma unroll
-    for (int e = 0; e < E; ++e) ph[e] = sw2[(SGN * (t + G * e)) & MASK];
-    // the group-FFT twiddles of this lane, in registers when they fit (at
-    // most 256 threads), else read from the table at each transform
-    constexpr bool RTW = THREADS <= 256 && !GB;
-    V twr[RTW ? E : 1];
-    if constexpr (RTW) {
-#pragma unroll
-      for (int k1 = 0; k1 < E; ++k1) twr[k1] = __ldg(&tw[k1 * G + t]);
-    }
+    // the group-FFT twiddles from registers (RTW), else from the table at
+    // each transform
     auto fft = [&](auto inv, V (&x)[E]) {
       if constexpr (RTW) group_fft_r<N, decltype(inv)::value>(x, scratch, twr, t);
       else group_fft<N, decltype(inv)::value>(x, scratch, tw, t);
@@ -413,6 +420,7 @@ __device__ __forceinline__ void tdst_plane(const SolveArgs<T>& a, int kz, unsign
   TDst<T, N, THREADS, ADJ, H16, GB> r(a, smem_raw);
   r.load_tables(a);
   __syncthreads();
+  r.lane_tables();
   r.plane(a, kz);
 }
 
@@ -428,6 +436,7 @@ __device__ __forceinline__ void tdst_persistent(const SolveArgs<T>& a, unsigned 
   }
   r.load_tables(a);
   __syncthreads();
+  r.lane_tables();
 #pragma unroll 1
   for (int kz = first; kz <= a.nz; kz += int(gridDim.x)) {
     const int next = kz + int(gridDim.x) <= a.nz ? kz + int(gridDim.x) : -1;

@@ -242,7 +242,15 @@ __device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsig
   V* scratch = sbase + (threadIdx.x / G) * GroupShape<L>::SSTRIDE;
 
   V v[E];
-  V xN;
+  const V bk = __ldg(&a.w2_z[2 * t + p]);
+  // Z(k) = X(k) + conj X(nz-k) + i w_{2nz}^{-k} (X(k) - conj X(nz-k)), k = 2(t+Ge)+p
+  auto rebuild = [&](V x, V xm_, int e) {
+    const V xm = cconj(xm_);
+    const V s = cadd(x, xm);
+    const V d = csub(x, xm);
+    const V wd = cmulc<true>(d, zphase<T, NZ>(a.w2_z, bk, 2 * (t + G * e) + p, e));   // w_{2nz}^{-k} d
+    return mk<V>(s.x - wd.y, s.y + wd.x);                      // s + i w d
+  };
   if constexpr (H16) {
     __half2* st16 = reinterpret_cast<__half2*>(smem_raw);
     const __half2* w16 = reinterpret_cast<const __half2*>(a.work);
@@ -264,7 +272,19 @@ __device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsig
     }
     const float2 f = __half22float2(mycol[NZ]);
     const float sc = __ldg(&rs[size_t(NZ) * a.nx]);
-    xN = mk<V>(T(f.x * sc), T(f.y * sc));
+    V xN = mk<V>(T(f.x * sc), T(f.y * sc));
+    __syncthreads();                                  // staging tile becomes FFT scratch
+    if (CONJ) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = cconj(v[e]);
+      xN = cconj(xN);
+    }
+    // partner X(nz - k) of every k = 2q + p (q = 0 pairs with X(nz))
+    V m[E];
+    mirror_fetch<L>(v, m, t, p, lane - t);
+    if (p == 0 && t == 0) m[0] = xN;
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = rebuild(v[e], m[e], e);
   } else {
     // the whole (nz+1) x COLS tile in flight at once (cp.async, one element each)
     for (int idx = threadIdx.x; idx < (NZ + 1) * Cfg::COLS; idx += Cfg::THREADS) {
@@ -274,29 +294,16 @@ __device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsig
     }
     cp_async_wait_all();
     __syncthreads();
+    // X(k) and its partner X(nz - k) straight from the staging tile (k = 0
+    // pairs with X(nz)), combined before the tile becomes FFT scratch
     const V* mycol = stage + col_local * Cfg::LDS;
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = mycol[2 * (t + G * e) + p];
-    xN = mycol[NZ];
-  }
-  __syncthreads();                                    // staging tile becomes FFT scratch
-  if (CONJ) {
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = cconj(v[e]);
-    xN = cconj(xN);
-  }
-  // partner X(nz - k) of every k = 2q + p (q = 0 pairs with X(nz))
-  V m[E];
-  mirror_fetch<L>(v, m, t, p, lane - t);
-  if (p == 0 && t == 0) m[0] = xN;
-  const V bk = __ldg(&a.w2_z[2 * t + p]);
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const V xm = cconj(m[e]);
-    const V s = cadd(v[e], xm);
-    const V d = csub(v[e], xm);
-    const V wd = cmulc<true>(d, zphase<T, NZ>(a.w2_z, bk, 2 * (t + G * e) + p, e));   // w_{2nz}^{-k} d, k = 2(t+Ge)+p
-    v[e] = mk<V>(s.x - wd.y, s.y + wd.x);                      // s + i w d
+    for (int e = 0; e < E; ++e) {
+      const int k = 2 * (t + G * e) + p;
+      const V x = mycol[k], xm = mycol[NZ - k];
+      v[e] = CONJ ? rebuild(cconj(x), cconj(xm), e) : rebuild(x, xm, e);
+    }
+    __syncthreads();                                  // staging tile becomes FFT scratch
   }
   zgroup_fft<L, true>(v, scratch, a.tw_z, t);                  // z_p(m), m = t + G e
   if (p) {
@@ -304,19 +311,21 @@ __device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsig
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = cmulc<true>(v[e], zphase<T, NZ>(a.w2_z, b, 2 * (t + G * e), e));
   }
+  // z(m) = z_0(m) + z_1(m): the lane of parity p keeps the sums for the slots
+  // e = j + p E/2; it sends its partner (lane t of the other parity) its own
+  // values of the partner's slots and adds what the partner sends back
+  V out[E / 2];
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    v[e].x += __shfl_xor_sync(0xffffffffu, v[e].x, G);
-    v[e].y += __shfl_xor_sync(0xffffffffu, v[e].y, G);
+  for (int j = 0; j < E / 2; ++j) {
+    const V snd = p ? v[j] : v[j + E / 2];
+    const V mine = p ? v[j + E / 2] : v[j];
+    out[j].x = mine.x + __shfl_xor_sync(0xffffffffu, snd.x, G);
+    out[j].y = mine.y + __shfl_xor_sync(0xffffffffu, snd.y, G);
   }
   if (valid) {
     V* dst = reinterpret_cast<V*>(a.phi + size_t(col) * NZ);
 #pragma unroll
-    for (int e2 = 0; e2 < E / 2; ++e2) {
-      const int e = e2 + p * (E / 2);
-      const V val = p ? v[e2 + E / 2] : v[e2];
-      dst[t + G * e] = val;
-    }
+    for (int j = 0; j < E / 2; ++j) dst[t + G * (j + p * (E / 2))] = out[j];
   }
 }
 
