@@ -290,6 +290,18 @@ int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_thread
  * undefined.  Errors: PIPE_EINVAL (null handle), PIPE_ECUDA. */
 int pipe_status(pipe_handle* h);
 
+/* Failure detection without a GPU fault, for tests: the next solve or
+ * adjoint of this handle (pipe_poisson_solve / _adjoint) whose transverse
+ * stage is the staged kernel (t_kind 2) has its first CTA leave out its bulk
+ * copy number drop_copy (0 = the first) and gives every wait at most
+ * poll_limit polls.  The wait for the left-out copy gives up, PIPE_ETIMEOUT
+ * is recorded (pipe_status), no further copy is issued by that CTA and the
+ * kernel still ends; the results of that call are undefined, later calls are
+ * unaffected.  The request is consumed by the next solve or adjoint whatever
+ * its plan.  Errors: PIPE_EINVAL (null handle, drop_copy < 0,
+ * poll_limit < 1). */
+int pipe_inject_stage_fault(pipe_handle* h, int drop_copy, long long poll_limit);
+
 /* Electric field E = -grad phi on the handle's mesh (device arrays of the
  * handle's dtype; FP32 for PIPE_F32_C16): phi [nx][ny][nz], E [3][nx][ny][nz]
  * (x, y, z components, each laid out like phi).  The paper defines no

@@ -201,6 +201,11 @@ class PipeSolver:
             check(st, "pipe_status")
         return st
 
+    def inject_stage_fault(self, drop_copy=0, poll_limit=4096):
+        """Failure-detection test hook (pipe_inject_stage_fault)."""
+        check(self.lib.pipe_inject_stage_fault(self.handle, int(drop_copy), int(poll_limit)),
+              "pipe_inject_stage_fault")
+
     def set_plan(self, z_warps=8, z_pipe=1, t_h=1, t_threads=256, t_kind=0):
         check(self.lib.pipe_set_plan(self.handle, int(z_warps), int(z_pipe), int(t_h), int(t_threads),
                                      int(t_kind)), "pipe_set_plan")

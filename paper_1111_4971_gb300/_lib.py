@@ -62,6 +62,7 @@ SIGNATURES = {
                               POINTER(c_int)]),
     "pipe_set_plan": (c_int, [H, c_int, c_int, c_int, c_int, c_int]),
     "pipe_status": (c_int, [H]),
+    "pipe_inject_stage_fault": (c_int, [H, c_int, ctypes.c_longlong]),
     "pipe_cic_deposit": (c_int, [H, c_void_p, c_int64, c_double, c_void_p, c_void_p]),
     "pipe_cic_gather_grad": (c_int, [H, c_void_p, c_int64, c_double, c_void_p, c_void_p, c_void_p]),
     "pipe_green_destroy": (None, [H]),

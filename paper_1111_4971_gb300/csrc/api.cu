@@ -179,6 +179,10 @@ cudaError_t transverse_stage(pipe_handle* h, bool adjoint, const SolveArgs<T>& a
 template <typename T>
 int run_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStream_t st) {
   SolveArgs<T> a = make_args<T>(h, rho, phi, h->work);
+  a.stage_drop = h->inject_drop;               // a pending failure-detection test
+  a.stage_polls = h->inject_polls;
+  h->inject_drop = 0;
+  h->inject_polls = 0;
   cudaError_t e;
   // the banded operator is symmetric: the adjoint is the same computation
   if (h->banded >= 0) return status_of(launch_banded<T>(h->plan.t_threads, a, h->banded, st));
@@ -413,6 +417,13 @@ int pipe_poisson_solve_host(pipe_handle* h, const void* rho_host, void* phi_host
   if ((e = cudaMemcpyAsync(phi_host, h->stage_phi, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return status_of(e);
   return status_of(cudaStreamSynchronize(st));
+}
+
+int pipe_inject_stage_fault(pipe_handle* h, int drop_copy, long long poll_limit) {
+  if (!h || drop_copy < 0 || poll_limit < 1) return PIPE_EINVAL;
+  h->inject_drop = drop_copy + 1;
+  h->inject_polls = poll_limit;
+  return PIPE_OK;
 }
 
 int pipe_status(pipe_handle* h) {

@@ -38,6 +38,8 @@ struct pipe_handle {
           *tw_t2c_64 = nullptr;
   void* tbuf = nullptr;        // n-point scratch planes (FP64 at 128 x 128), see SolveArgs::tbuf
   int* err = nullptr;          // device error word (in the tab32 allocation), see pipe_status
+  int inject_drop = 0;         // pipe_inject_stage_fault: consumed by the next solve
+  long long inject_polls = 0;
   void* stage_rho = nullptr;   // device staging for pipe_poisson_solve_host
   void* stage_phi = nullptr;
   // pipe_poisson_solve_host_stream: two device staging buffers per direction,

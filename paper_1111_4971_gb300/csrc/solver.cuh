@@ -38,6 +38,11 @@ struct SolveArgs {
   // device error word of the handle (PIPE_ETIMEOUT when a bounded wait of the
   // staged transverse kernel gave up); null: not recorded
   int* err;
+  // failure-detection tests of the staged transverse kernel: its first CTA
+  // leaves out bulk copy number stage_drop - 1 (0: none) and every wait polls
+  // at most stage_polls times (0: the default limit)
+  int stage_drop;
+  long long stage_polls;
 };
 
 // z transforms: one CTA handles COLS consecutive (i,j) columns.

@@ -72,7 +72,7 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 // polls of a staged-row wait before it gives up (about 0.2 s with the back-off)
-constexpr long kStageSpinLimit = 1L << 21;
+constexpr long long kStageSpinLimit = 1LL << 21;
 
 // GB: the plane buffer in a global scratch plane (a.tbuf, L2-resident)
 // instead of shared memory, for planes too large for it (FP64 128 x 128).
@@ -135,6 +135,7 @@ struct TDst {
   V twr[RTW ? E : 1];
   unsigned sphase = 0;        // STG: parity of the next staged chunk
   bool sfail = false;         // STG: a wait gave up (PIPE_ETIMEOUT recorded)
+  int nissued = 0;            // STG, issuing thread: bulk copies issued so far
   int lane, t, line;
 
   __device__ __forceinline__ TDst(const SolveArgs<T>& a, unsigned char* smem_raw) {
@@ -150,8 +151,13 @@ struct TDst {
   }
 
   // STG, one thread: copy rows r0 .. r0+SR-1 of plane kz into the staging
-  // buffer (the caller has synchronised after the buffer's last reads)
+  // buffer (the caller has synchronised after the buffer's last reads).  No
+  // copy is issued once this thread's own wait has given up, and the copy
+  // that a failure-detection test asks CTA 0 to leave out is skipped.
   __device__ __forceinline__ void stage_issue(const SolveArgs<T>& a, int kz, int r0) {
+    const bool drop = blockIdx.x == 0 && nissued + 1 == a.stage_drop;
+    ++nissued;
+    if (sfail || drop) return;
     fence_async_smem();
     bulk_load(stg, a.work + (size_t(kz) * N + r0) * N, unsigned(Cfg::STG_BYTES), bar);
   }
@@ -160,9 +166,10 @@ struct TDst {
   // PIPE_ETIMEOUT and later waits return at once, so the kernel always ends
   __device__ __forceinline__ void stage_wait(const SolveArgs<T>& a) {
     if (!sfail) {
-      long polls = 0;
+      const long long limit = a.stage_polls > 0 ? a.stage_polls : kStageSpinLimit;
+      long long polls = 0;
       while (!mbar_test(bar, sphase)) {
-        if (++polls > kStageSpinLimit) {
+        if (++polls > limit) {
           sfail = true;
           if (a.err) atomicExch(a.err, PIPE_ETIMEOUT);
           break;
@@ -446,7 +453,8 @@ __device__ __forceinline__ void tdst_persistent(const SolveArgs<T>& a, unsigned 
   // after a wait gave up a copy may still be in flight: wait for it (bounded)
   // so that it does not land after the CTA has left
   if (threadIdx.x == 0 && r.sfail) {
-    for (long polls = 0; polls < kStageSpinLimit && !mbar_test(r.bar, r.sphase); ++polls) __nanosleep(64);
+    const long long limit = a.stage_polls > 0 ? a.stage_polls : kStageSpinLimit;
+    for (long long polls = 0; polls < limit && !mbar_test(r.bar, r.sphase); ++polls) __nanosleep(64);
   }
 }
 

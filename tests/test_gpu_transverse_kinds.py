@@ -138,3 +138,25 @@ def test_npoint_plan_refused_where_it_does_not_apply():
     s = solver(geom, grid, 1, torch.float32)
     with pytest.raises(PipeError):
         s.set_plan(z_warps=8, z_pipe=0, t_h=1, t_threads=256, t_kind=2)
+
+
+def test_staged_wait_gives_up_records_timeout_and_recovers():
+    """Failure detection without a GPU fault: the first CTA leaves out one of
+    its own bulk copies, so its wait has nothing to wait for.  The bounded
+    wait gives up, PIPE_ETIMEOUT reaches the host through pipe_status, the
+    kernel still ends, and the next solve is exact again."""
+    from paper_1111_4971_gb300 import _lib
+    geom, grid = CELL["sq128x128x32"]
+    s = solver(geom, grid, 1, torch.float32)
+    _plan(s, 256, 2)
+    x = dev(random_density(grid.shape, 7, sparsity=0.2), torch.float32)
+    want = host(s.solve(x))
+    assert s.status() == _lib.PIPE_OK
+    for drop in (0, 2):                    # the first plane's first copy; a later one
+        s.inject_stage_fault(drop_copy=drop, poll_limit=2048)
+        s.solve(x)
+        torch.cuda.synchronize()
+        assert s.status() == _lib.PIPE_ETIMEOUT
+        assert s.status() == _lib.PIPE_OK                # read and cleared
+        assert np.array_equal(host(s.solve(x)), want)
+        assert s.status() == _lib.PIPE_OK
