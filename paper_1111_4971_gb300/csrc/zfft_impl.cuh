@@ -286,21 +286,33 @@ __device__ __forceinline__ void zinv_tile(const SolveArgs<T>& a, int tile, unsig
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = rebuild(v[e], m[e], e);
   } else {
-    // the whole (nz+1) x COLS tile in flight at once (cp.async, one element each)
-    for (int idx = threadIdx.x; idx < (NZ + 1) * Cfg::COLS; idx += Cfg::THREADS) {
-      const int r = idx / Cfg::COLS;
-      const int cc = idx % Cfg::COLS;
-      if (col0 + cc < ncols) cp_async_elem(&stage[cc * Cfg::LDS + r], &a.work[size_t(r) * ncols + col0 + cc]);
+    // the whole (nz+1) x COLS tile in flight at once (cp.async, one element
+    // each); a column holds its even kz in slots 0..nz/2 and its odd kz after
+    // them, so that the lanes of one parity read consecutive slots
+    // (thread: column cc, rows r0, r0 + RSTEP, ...; RSTEP = 2G is even, so
+    // the row parity and hence the half of the column are fixed per thread)
+    {
+      constexpr int RSTEP = Cfg::THREADS / Cfg::COLS;
+      static_assert(RSTEP % 2 == 0, "row step keeps the parity");
+      const int cc = threadIdx.x % Cfg::COLS, r0 = threadIdx.x / Cfg::COLS;
+      if (col0 + cc < ncols) {
+        V* dst = stage + cc * Cfg::LDS + ((r0 & 1) ? NZ / 2 + 1 : 0) + (r0 >> 1);
+        const V* src = a.work + size_t(r0) * ncols + col0 + cc;
+        for (int r = r0; r <= NZ; r += RSTEP, dst += RSTEP / 2, src += size_t(RSTEP) * ncols)
+          cp_async_elem(dst, src);
+      }
     }
     cp_async_wait_all();
     __syncthreads();
     // X(k) and its partner X(nz - k) straight from the staging tile (k = 0
-    // pairs with X(nz)), combined before the tile becomes FFT scratch
-    const V* mycol = stage + col_local * Cfg::LDS;
+    // pairs with X(nz)), combined before the tile becomes FFT scratch:
+    // k = 2(t + G e) + p sits in slot (p ? nz/2 + 1 : 0) + t + G e, and
+    // nz - k in slot (p ? nz : nz/2) - t - G e
+    const V* mine = stage + col_local * Cfg::LDS + (p ? NZ / 2 + 1 : 0) + t;
+    const V* mirr = stage + col_local * Cfg::LDS + (p ? NZ : NZ / 2) - t;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int k = 2 * (t + G * e) + p;
-      const V x = mycol[k], xm = mycol[NZ - k];
+      const V x = mine[G * e], xm = mirr[-G * e];
       v[e] = CONJ ? rebuild(cconj(x), cconj(xm), e) : rebuild(x, xm, e);
     }
     __syncthreads();                                  // staging tile becomes FFT scratch
