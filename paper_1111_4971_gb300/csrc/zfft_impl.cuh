@@ -110,6 +110,101 @@ __device__ __forceinline__ void zgroup_fft(V (&v)[GroupShape<L>::E], V* scratch,
   else group_fft<L, INV>(v, scratch, tw, t);
 }
 
+// Real-to-complex pairing of the forward z transform.  Slot e of lane (t, p)
+// holds Z(k), k = 2(t + G e) + p; its mirror Z(nz - k) is slot E-1-e of lane
+// G-1-t (odd half) or lane (G-t) mod G (even half), except in lane t = 0 of
+// the even half, which holds both members of its pairs itself (slots e and
+// E-e; slot 0 pairs with itself through Z(nz) = Z(0), and slot E/2 is
+// k = nz/2).  Every lane computes X(k) and X(nz - k) for its slots e < E/2,
+// so it needs only the partner's slots E/2 .. E-1: half of the values cross
+// lanes.  X(k) = (Z(k) + conj Z(nz-k) - i w^k (Z(k) - conj Z(nz-k))) / 2 with
+// w = w_{2nz}; X(nz - k) swaps the pair and takes w^{nz-k} = -conj(w^k)
+// (X(nz) = Re Z(0) - Im Z(0) is the case k = 0).  xh: X(nz/2), in lane t = 0
+// of the even half only.
+template <typename T, int NZ, int WARPS, bool CONJ>
+__device__ __forceinline__ void zfwd_pairs(const SolveArgs<T>& a, const C2<T> (&v)[GroupShape<NZ / 2>::E], int t,
+                                           int p, int lane, C2<T> (&xa)[GroupShape<NZ / 2>::E / 2],
+                                           C2<T> (&xb)[GroupShape<NZ / 2>::E / 2], C2<T>& xh) {
+  using V = C2<T>;
+  constexpr int G = GroupShape<NZ / 2>::G, E = GroupShape<NZ / 2>::E;
+  const bool zero_lane = (p == 0) && (t == 0);
+  const int partner = (lane - t) + (p == 0 ? ((G - t) & (G - 1)) : (G - 1 - t));
+  V zm[E / 2];                                        // Z(nz - k) of slot j
+#pragma unroll
+  for (int j = 0; j < E / 2; ++j) {
+    const V snd = v[E - 1 - j];
+    V r;
+    r.x = __shfl_sync(0xffffffffu, snd.x, partner);
+    r.y = __shfl_sync(0xffffffffu, snd.y, partner);
+    zm[j] = zero_lane ? v[(E - j) % E] : r;
+  }
+  const V bk = __ldg(&a.w2_z[2 * t + p]);
+  auto r2c = [](V z, V zmir, V w) {
+    const V zc = cconj(zmir);
+    const V s = cadd(z, zc);
+    const V d = csub(z, zc);
+    const V wd = cmul(w, d);
+    const V x = mk<V>(T(0.5) * (s.x + wd.y), T(0.5) * (s.y - wd.x));   // (s - i w d)/2
+    return CONJ ? cconj(x) : x;
+  };
+#pragma unroll
+  for (int j = 0; j < E / 2; ++j) {
+    const V w = zphase<T, NZ>(a.w2_z, bk, 2 * (t + G * j) + p, j);
+    xa[j] = r2c(v[j], zm[j], w);
+    xb[j] = r2c(zm[j], v[j], mk<V>(-w.x, w.y));
+  }
+  xh = zero_lane ? r2c(v[E / 2], v[E / 2], zphase<T, NZ>(a.w2_z, bk, G * E, E / 2)) : mk<V>(T(0), T(0));
+}
+
+// The staging column of the forward z transform holds its even kz in slots
+// 0..nz/2 and its odd kz after them, so that the lanes of one parity write
+// consecutive slots: k = 2(t + G j) + p goes to slot (p ? nz/2 + 1 : 0) + t + G j,
+// nz - k to slot (p ? nz : nz/2) - t - G j, and nz/2 to slot nz/4.
+template <typename T, int NZ>
+__device__ __forceinline__ void zfwd_stage_col(C2<T>* col, const C2<T> (&xa)[GroupShape<NZ / 2>::E / 2],
+                                               const C2<T> (&xb)[GroupShape<NZ / 2>::E / 2], C2<T> xh, int t,
+                                               int p) {
+  constexpr int G = GroupShape<NZ / 2>::G, E = GroupShape<NZ / 2>::E;
+  C2<T>* mine = col + (p ? NZ / 2 + 1 : 0) + t;
+  C2<T>* mirr = col + (p ? NZ : NZ / 2) - t;
+#pragma unroll
+  for (int j = 0; j < E / 2; ++j) {
+    mine[G * j] = xa[j];
+    mirr[-G * j] = xb[j];
+  }
+  if (p == 0 && t == 0) col[NZ / 4] = xh;
+}
+
+// Coalesced 16-byte stores (EPV complex of consecutive columns) of a staged
+// tile into work[kz][col0 ..].  Thread (q0, cc) takes rows r0, r0 + QSTEP, ...,
+// where r0 orders each block of 8 rows as 0 2 4 6 1 3 5 7, so that the two
+// half-warps read rows of one parity each (conflict-free) and the row parity
+// is fixed per thread.
+template <typename T, int NZ, int WARPS>
+__device__ __forceinline__ void zfwd_store_tile(const SolveArgs<T>& a, const C2<T>* stage, int col0) {
+  using Cfg = ZCfg<T, NZ, WARPS>;
+  using V = C2<T>;
+  constexpr int EPV = 16 / int(sizeof(V));
+  constexpr int VPR = Cfg::COLS / EPV;
+  constexpr int QSTEP = Cfg::THREADS / VPR;
+  static_assert(QSTEP % 8 == 0 && NZ % 8 == 0, "rows in blocks of 8");
+  const int ncols = a.nx * a.ny;
+  const int q0 = threadIdx.x / VPR;
+  const int cc = (threadIdx.x % VPR) * EPV;
+  const int r0 = (q0 & ~7) | ((q0 & 3) << 1) | ((q0 >> 2) & 1);
+  if (col0 + cc >= ncols) return;
+  const V* src = stage + cc * Cfg::LDS + ((r0 & 1) ? NZ / 2 + 1 : 0) + (r0 >> 1);
+  V* dst = a.work + size_t(r0) * ncols + col0 + cc;
+  for (int r = r0; r <= NZ; r += QSTEP, src += QSTEP / 2, dst += size_t(QSTEP) * ncols) {
+    if constexpr (EPV == 2) {
+      const V x0 = src[0], x1 = src[Cfg::LDS];
+      *reinterpret_cast<float4*>(dst) = make_float4(x0.x, x0.y, x1.x, x1.y);
+    } else {
+      *dst = src[0];
+    }
+  }
+}
+
 // one CTA of 32*WARPS threads: columns [tile*COLS, (tile+1)*COLS)
 // H16: the spectrum is stored as complex FP16 with one scale per tile
 // (a.zscale[tile]); the reduction scratch follows Cfg::smem_bytes().
@@ -143,34 +238,18 @@ __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsig
     for (int e = 0; e < E; ++e) v[e] = cmul(v[e], zphase<T, NZ>(a.w2_z, b, 2 * (t + G * e), e));   // w_nz^m
   }
   zgroup_fft<L, false>(v, scratch, a.tw_z, t);        // v[e] = Z(2q + p), q = t + G e
-  const V z0 = v[0];
-  V m[E];
-  mirror_fetch<L>(v, m, t, p, lane - t);
-  const V bk = __ldg(&a.w2_z[2 * t + p]);
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const V zc = cconj(m[e]);
-    const V s = cadd(v[e], zc);
-    const V d = csub(v[e], zc);
-    const V wd = cmul(zphase<T, NZ>(a.w2_z, bk, 2 * (t + G * e) + p, e), d);           // w_{2nz}^k d, k = 2(t+Ge)+p
-    V x = mk<V>(T(0.5) * (s.x + wd.y), T(0.5) * (s.y - wd.x));   // (s - i w d)/2
-    v[e] = CONJ ? cconj(x) : x;
-  }
-  // X(nz) = Re Z(0) - Im Z(0), held by lane t=0 of the even half
-  const V xN = mk<V>(z0.x - z0.y, T(0));
-
-  // staged, coalesced stores of the whole (nz+1) x COLS tile
+  V xa[E / 2], xb[E / 2], xh;
+  zfwd_pairs<T, NZ, WARPS, CONJ>(a, v, t, p, lane, xa, xb, xh);
   __syncthreads();                                    // FFT scratch becomes the staging tile
-  V* mycol = stage + col_local * Cfg::LDS;
-#pragma unroll
-  for (int e = 0; e < E; ++e) mycol[2 * (t + G * e) + p] = v[e];
-  if (p == 0 && t == 0) mycol[NZ] = CONJ ? cconj(xN) : xN;
+  zfwd_stage_col<T, NZ>(stage + col_local * Cfg::LDS, xa, xb, xh, t, p);
   if constexpr (H16) {
     float* red = reinterpret_cast<float*>(smem_raw + Cfg::smem_bytes());
-    float mx = 0.f;
+    float mx = fmaxf(fabsf(float(xh.x)), fabsf(float(xh.y)));
 #pragma unroll
-    for (int e = 0; e < E; ++e) mx = fmaxf(mx, fmaxf(fabsf(float(v[e].x)), fabsf(float(v[e].y))));
-    if (p == 0 && t == 0) mx = fmaxf(mx, fabsf(float(xN.x)));
+    for (int j = 0; j < E / 2; ++j) {
+      mx = fmaxf(mx, fmaxf(fabsf(float(xa[j].x)), fabsf(float(xa[j].y))));
+      mx = fmaxf(mx, fmaxf(fabsf(float(xb[j].x)), fabsf(float(xb[j].y))));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) red[warp] = mx;
@@ -179,6 +258,7 @@ __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsig
 #pragma unroll
     for (int w = 0; w < WARPS; ++w) mx = fmaxf(mx, red[w]);
     const float sc = slab_scale(mx), inv = 1.f / sc;
+    auto slot = [](int k) { return (k & 1) ? NZ / 2 + 1 + (k >> 1) : (k >> 1); };
     if (threadIdx.x == 0) a.zscale[tile] = sc;
     // 16-byte stores of four complex-FP16 values (consecutive columns)
     constexpr int VPR = Cfg::COLS / 4;
@@ -194,7 +274,7 @@ __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsig
         } pk;                                       // 16-byte aligned by its uint4 member
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const V x = stage[(cc + q) * Cfg::LDS + r];
+          const V x = stage[(cc + q) * Cfg::LDS + slot(r)];
           pk.h[q] = __floats2half2_rn(float(x.x) * inv, float(x.y) * inv);
         }
         *reinterpret_cast<uint4*>(&w16[size_t(r) * ncols + col0 + cc]) = pk.u;
@@ -203,21 +283,7 @@ __device__ __forceinline__ void zfwd_tile(const SolveArgs<T>& a, int tile, unsig
     return;
   }
   __syncthreads();
-  // 16-byte stores: EPV complex (consecutive columns) per vector
-  constexpr int EPV = 16 / int(sizeof(V));
-  constexpr int VPR = Cfg::COLS / EPV;
-  for (int idx = threadIdx.x; idx < (NZ + 1) * VPR; idx += Cfg::THREADS) {
-    const int r = idx / VPR;
-    const int cc = (idx % VPR) * EPV;
-    if (col0 + cc < ncols) {
-      if constexpr (EPV == 2) {
-        const V x0 = stage[cc * Cfg::LDS + r], x1 = stage[(cc + 1) * Cfg::LDS + r];
-        *reinterpret_cast<float4*>(&a.work[size_t(r) * ncols + col0 + cc]) = make_float4(x0.x, x0.y, x1.x, x1.y);
-      } else {
-        a.work[size_t(r) * ncols + col0 + cc] = stage[cc * Cfg::LDS + r];
-      }
-    }
-  }
+  zfwd_store_tile<T, NZ, WARPS>(a, stage, col0);
 }
 
 // H16: the spectrum is complex FP16 with one scale per transverse row
@@ -396,41 +462,11 @@ __device__ __forceinline__ void zfwd_tiles_pipe(const SolveArgs<T>& a, int first
       for (int e = 0; e < E; ++e) v[e] = cmul(v[e], zphase<T, NZ>(a.w2_z, b, 2 * (t + G * e), e));
     }
     zgroup_fft<L, false>(v, scratch, a.tw_z, t);
-    const V z0 = v[0];
-    V m[E];
-    mirror_fetch<L>(v, m, t, p, lane - t);
-    V* mycol = stage + col_local * Cfg::LDS;
-    const V bk = __ldg(&a.w2_z[2 * t + p]);
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int kz = 2 * (t + G * e) + p;
-      const V zc = cconj(m[e]);
-      const V s = cadd(v[e], zc);
-      const V d = csub(v[e], zc);
-      const V wd = cmul(zphase<T, NZ>(a.w2_z, bk, 2 * (t + G * e) + p, e), d);
-      V x = mk<V>(T(0.5) * (s.x + wd.y), T(0.5) * (s.y - wd.x));
-      mycol[kz] = CONJ ? cconj(x) : x;
-    }
-    if (p == 0 && t == 0) {
-      const V xN = mk<V>(z0.x - z0.y, T(0));
-      mycol[NZ] = CONJ ? cconj(xN) : xN;
-    }
+    V xa[E / 2], xb[E / 2], xh;
+    zfwd_pairs<T, NZ, WARPS, CONJ>(a, v, t, p, lane, xa, xb, xh);
+    zfwd_stage_col<T, NZ>(stage + col_local * Cfg::LDS, xa, xb, xh, t, p);
     __syncthreads();
-    constexpr int EPV = 16 / int(sizeof(V));
-    constexpr int VPR = Cfg::COLS / EPV;
-    for (int idx = threadIdx.x; idx < (NZ + 1) * VPR; idx += Cfg::THREADS) {
-      const int r = idx / VPR;
-      const int cc = (idx % VPR) * EPV;
-      if (col0 + cc < ncols) {
-        if constexpr (EPV == 2) {
-          const V x0 = stage[cc * Cfg::LDS + r], x1 = stage[(cc + 1) * Cfg::LDS + r];
-          *reinterpret_cast<float4*>(&a.work[size_t(r) * ncols + col0 + cc]) =
-              make_float4(x0.x, x0.y, x1.x, x1.y);
-        } else {
-          a.work[size_t(r) * ncols + col0 + cc] = stage[cc * Cfg::LDS + r];
-        }
-      }
-    }
+    zfwd_store_tile<T, NZ, WARPS>(a, stage, col0);
     __syncthreads();
   }
 }
