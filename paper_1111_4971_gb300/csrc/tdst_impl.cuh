@@ -213,6 +213,39 @@ struct TDst {
     return x;
   }
 
+  // Mirror pairs of an N-point spectrum in the cyclic layout (lane t holds
+  // q = t + G e): the mirror N - q of slot e is slot E-1-e of lane (G-t) mod G,
+  // except in lane 0, whose slots e and E-e are each other's mirrors (slot 0,
+  // q = 0, and slot E/2, q = N/2, are their own).  Each lane works on the
+  // pairs of its slots j < E/2, so half of the values cross lanes.
+  // pair_fetch: the mirror values of the slots j < E/2.
+  __device__ __forceinline__ void pair_fetch(const V (&x)[E], V (&xm)[H]) const {
+    const int src = (lane - t) + ((G - t) & (G - 1));
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const V snd = x[E - 1 - j];
+      V r;
+      r.x = __shfl_sync(0xffffffffu, snd.x, src);
+      r.y = __shfl_sync(0xffffffffu, snd.y, src);
+      xm[j] = t == 0 ? x[(E - j) % E] : r;
+    }
+  }
+  // pair_return: from results at the slots j < E/2 (ra) and at their mirrors
+  // (rb; lane 0: rb[0] unused, rh at its slot E/2), the cyclic layout again
+  // (slot E-1-j of lane t is the mirror of slot j of lane (G-t) mod G)
+  __device__ __forceinline__ void pair_return(const V (&ra)[H], const V (&rb)[H], V rh, V (&x)[E]) const {
+    const int src = (lane - t) + ((G - t) & (G - 1));
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      x[j] = ra[j];
+      V r;
+      r.x = __shfl_sync(0xffffffffu, rb[j].x, src);
+      r.y = __shfl_sync(0xffffffffu, rb[j].y, src);
+      const V own = (j + 1 < H) ? rb[j + 1 < H ? j + 1 : 0] : rh;   // lane 0
+      x[E - 1 - j] = t == 0 ? own : r;
+    }
+  }
+
   // load_row for complex-FP16 planes: values times their z-tile scale
   __device__ __forceinline__ void load_row16(const SolveArgs<T>& a, int kz, int il, V (&v)[E]) const {
     const int i = il < N ? il : 0;
@@ -280,15 +313,22 @@ struct TDst {
         load_row(pl, il, v);
       }
       fft(Fwd{}, v);                   // V(q)
-      V m[E];
-      mirror_fetch<N>(v, m, t, 0, lane - t);                   // V(N-q)
+      V vm[H];
+      pair_fetch(v, vm);               // V(N-q) of the slots j < E/2
       if (il < N) {
+        // U(q) = V(q) - w^{-q} V(N-q), U(N-q) = V(N-q) + conj(w^{-q}) V(q)
+        // (w^{-(N-q)} = -conj(w^{-q})); lane 0: U(N) = 2 V(0), and q = N/2
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int q = t + G * e;
-          if (q == 0) ybuf[tile(N, il)] = mk<V>(v[e].x + v[e].x, v[e].y + v[e].y);
-          else ybuf[tile(q, il)] = cfms(v[e], ph[e], m[e]);
+        for (int j = 0; j < H; ++j) {
+          const int q = t + G * j;
+          if (q == 0) {
+            ybuf[tile(N, il)] = mk<V>(v[0].x + v[0].x, v[0].y + v[0].y);
+          } else {
+            ybuf[tile(q, il)] = cfms(v[j], ph[j], vm[j]);
+            ybuf[tile(N - q, il)] = cfms(vm[j], mk<V>(-ph[j].x, ph[j].y), v[j]);
+          }
         }
+        if (t == 0) ybuf[tile(N / 2, il)] = cfms(v[H], ph[H], v[H]);
       }
     }
     __syncthreads();
@@ -311,26 +351,54 @@ struct TDst {
         }
       }
       const T* grow = a.green + (size_t(kz) * (N + 1) + ky) * (N + 1);
-      T gpre[E];                       // the Green row, read before the transform
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int kx = t + G * e;
-        gpre[e] = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
-      }
-      fft(Fwd{}, u);                   // V(kx)
-      V m[E];
-      mirror_fetch<N>(u, m, t, 0, lane - t);
       if constexpr (!H16) {
+        // the Green row at kx = q_j (N for q_j = 0) and N - q_j of the slots
+        // j < E/2, and at N/2 (lane 0), read before the transform
+        T ga[H], gb[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+          const int kx = t + G * j;
+          ga[j] = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
+          gb[j] = act ? __ldg(&grow[N - kx]) : T(0);
+        }
+        const T gh = act ? __ldg(&grow[N / 2]) : T(0);
+        fft(Fwd{}, u);                 // V(kx)
+        V um[H];
+        pair_fetch(u, um);             // V(N-kx) of the slots j < E/2
+        // P = g U at kx and N - kx, then V'(q) = P(q) + w^{-q} P(N-q) and
+        // V'(N-q) = P(N-q) - conj(w^{-q}) P(q); lane 0: V'(0) = P(N) with
+        // U(N) = 2 V(0), and the self-mirrored kx = N/2
+        V ra[H], rb[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+          const int kx = t + G * j;
+          const V nph = mk<V>(-ph[j].x, ph[j].y);
+          if (kx == 0) {
+            ra[j] = cscale(mk<V>(u[0].x + u[0].x, u[0].y + u[0].y), ga[j]);
+            rb[j] = ra[j];
+          } else {
+            const V pa = cscale(cfms(u[j], ph[j], um[j]), ga[j]);
+            const V pb = cscale(cfms(um[j], nph, u[j]), gb[j]);
+            ra[j] = cfma_(pa, ph[j], pb);
+            rb[j] = cfma_(pb, nph, pa);
+          }
+        }
+        V rh = mk<V>(T(0), T(0));
+        if (t == 0) {
+          const V pn = cscale(cfms(u[H], ph[H], u[H]), gh);
+          rh = cfma_(pn, ph[H], pn);
+        }
+        pair_return(ra, rb, rh, u);    // V'(q) in the cyclic layout
+      } else {
+        T gpre[E];                     // the Green row, read before the transform
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int kx = t + G * e;
-          const T g = gpre[e];
-          // slot 0 carries kx = N: U(N) = 2 V(0)
-          const V w = (kx == 0) ? mk<V>(u[e].x + u[e].x, u[e].y + u[e].y)
-                                : cfms(u[e], ph[e], m[e]);
-          u[e] = cscale(w, g);                                 // P(kx)
+          gpre[e] = act ? __ldg(&grow[kx == 0 ? N : kx]) : T(0);
         }
-      } else {
+        fft(Fwd{}, u);                 // V(kx)
+        V m[E];
+        mirror_fetch<N>(u, m, t, 0, lane - t);
         // complex-FP16 product: both operands scaled per column so that
         // their largest magnitude is 2^7 (the product stays below 2^14)
         float g[E];
@@ -351,16 +419,16 @@ struct TDst {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const __half2 uh = __floats2half2_rn(float(u[e].x) * iu, float(u[e].y) * iu);
-          const __half2 ph = __hmul2(uh, __float2half2_rn(g[e] * ig));
-          const float2 pf = __half22float2(ph);
+          const __half2 hp = __hmul2(uh, __float2half2_rn(g[e] * ig));
+          const float2 pf = __half22float2(hp);
           u[e] = mk<V>(T(pf.x * back), T(pf.y * back));       // P(kx)
         }
-      }
-      mirror_fetch<N>(u, m, t, 0, lane - t);                   // P(N-kx)
+        mirror_fetch<N>(u, m, t, 0, lane - t);                 // P(N-kx)
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int q = t + G * e;
-        if (q != 0) u[e] = cfma_(u[e], ph[e], m[e]);   // V'(q); V'(0) = P(N)
+        for (int e = 0; e < E; ++e) {
+          const int q = t + G * e;
+          if (q != 0) u[e] = cfma_(u[e], ph[e], m[e]);         // V'(q); V'(0) = P(N)
+        }
       }
       fft(Bwd{}, u);                   // even samples 2n of the column
       if (act) {
