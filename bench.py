@@ -40,7 +40,7 @@ KERNEL_SOURCES = {
     "z_inverse": ["zfft_impl.cuh", "zfft.cu", "fft_common.cuh", "solver.cuh"],
 }
 PROFILE_FILES = {
-    "transverse": "transverse_dst_pipe128x128x1024_igf_f32.md",
+    "transverse": "transverse_dsts_pipe128x128x1024_igf_f32.md",
     "z_forward": "zfft_pipe128x128x1024_igf_f32.md",
     "z_inverse": "zfft_pipe128x128x1024_igf_f32.md",
 }
