@@ -23,11 +23,15 @@
 // therefore costs one N-point transform plus a mirror combination of the
 // pairs (q, N-q), instead of a 2N-point transform with half its inputs zero.
 //
-// Layout and schedule are those of the cyclic 2N-point routine: one CTA per
-// kz plane, lanes of a group of G hold elements q = t + G e; pass 1 transforms
-// the N rows along y into the ky = 1..N columns of a shared-memory buffer,
-// pass 2 transforms each column along x, multiplies by the Green octant,
-// transforms back and stores it in place, pass 3 transforms the rows back.
+// Layout and schedule are those of the cyclic 2N-point routine: lanes of a
+// group of G hold elements q = t + G e; pass 1 transforms the N rows along y
+// into the ky = 1..N columns of a shared-memory buffer, pass 2 transforms each
+// column along x, multiplies by the Green octant, transforms back and stores
+// it in place, pass 3 transforms the rows back.  The pairs (q, N-q) of the
+// mirror combinations are formed by the lane holding q for the first half of
+// its slots, so half of the values cross lanes.  tdst_plane runs one plane
+// per CTA; tdst_persistent is the staged form, one CTA per SM looping over
+// planes, its pass-1 rows arriving by TMA bulk copies.
 #pragma once
 
 #include "../../include/pipe_poisson.h"
