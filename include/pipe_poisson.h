@@ -261,9 +261,10 @@ int pipe_stage_z_inverse(pipe_handle* h, const void* spec, void* phi, int adjoin
  * appended to it. */
 int pipe_autotune(pipe_handle* h, void* stream);
 
-/* Read or pin the kernel variants a handle uses: z_warps in {8, 16} (CTA size of
- * the z transforms), z_pipe in {0, 1} (1: each z CTA walks several tiles and
- * streams the next tile's input while transforming the current one), t_h in
+/* Read or pin the kernel variants a handle uses: z_warps in {4, 8, 16} (CTA
+ * size of the z transforms; 4 and 16 apply at nz >= 512, smaller nz run 8),
+ * z_pipe in {0, 1} (1: each z CTA walks several tiles and streams the next
+ * tile's input while transforming the current one), t_h in
  * {1, 2, 4} (the transverse stage runs t_h CTAs per kz plane, each holding
  * nx/t_h rows), t_threads in {128, 256, 512}, t_kind in {0, 1, 2}: 0 computes
  * each transverse line with the padded 2n-point transforms of Eq. 10 (any

@@ -22,11 +22,12 @@ namespace pp {
 
 Plan default_plan(int n, int nz, bool f64, bool cell_centred) {
   Plan p;
-  // timed on GB300: FP32 one CTA per plane, on cell-centred meshes with the
-  // n-point routine (256 threads; 512 at n = 64; at n = 128 its staged
-  // persistent form), else the cyclic 2n-point routine (512 threads); FP64
-  // 2-CTA clusters of 128 threads at n = 128
-  p.z_warps = 8;
+  // timed on GB300: FP32 z transforms in 4-warp CTAs where a column fills
+  // a warp (nz >= 512), else 8; FP32 one CTA per plane, on cell-centred
+  // meshes with the n-point routine (256 threads; 512 at n = 64; at n = 128
+  // its staged persistent form), else the cyclic 2n-point routine (512
+  // threads); FP64 2-CTA clusters of 128 threads at n = 128
+  p.z_warps = (!f64 && nz >= 512) ? 4 : 8;
   p.z_pipe = 0;
   p.t_kind = 0;
   if (!f64) {
@@ -160,7 +161,7 @@ int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
     *out = best;
     return PIPE_OK;
   }
-  for (int zw : {8, 16})
+  for (int zw : {4, 8, 16})
     for (int zp : {0, 1}) {
       float ms = time_ms([&] {
         cudaError_t e = launch_z<T>(true, zw, zp, false, a, st);
@@ -252,7 +253,7 @@ extern "C" int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h
 
 extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads, int t_kind) {
   if (!h) return PIPE_EINVAL;
-  if ((z_warps != 8 && z_warps != 16) || (z_pipe != 0 && z_pipe != 1) || (t_h != 1 && t_h != 2 && t_h != 4) ||
+  if ((z_warps != 4 && z_warps != 8 && z_warps != 16) || (z_pipe != 0 && z_pipe != 1) || (t_h != 1 && t_h != 2 && t_h != 4) ||
       (t_threads != 128 && t_threads != 256 && t_threads != 512) || t_kind < 0 || t_kind > 2)
     return PIPE_EINVAL;
   if (t_kind >= 1) {

@@ -4,17 +4,22 @@
 
 namespace pp {
 
+// CTAs of the single-tile z kernels resident per SM (their register cap:
+// 128 per thread at 4 and 8 warps per CTA)
+template <int WARPS>
+constexpr int z_ctas_per_sm() { return WARPS <= 4 ? 4 : (WARPS <= 8 ? 2 : 1); }
+
 // The tile that a CTA of the next wave will take: this tile plus the number
 // of CTAs resident at once (SMs x CTAs per SM), blocks being issued in order.
 template <int WARPS>
 __device__ __forceinline__ int next_wave_tile() {
   unsigned nsm;
   asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
-  return int(blockIdx.x) + int(nsm) * (WARPS <= 8 ? 2 : 1);
+  return int(blockIdx.x) + int(nsm) * z_ctas_per_sm<WARPS>();
 }
 
 template <typename T, int NZ, int WARPS, bool CONJ, bool H16>
-__global__ void __launch_bounds__(32 * WARPS, (WARPS <= 8 ? 2 : 1)) zfwd_kernel(SolveArgs<T> a) {
+__global__ void __launch_bounds__(32 * WARPS, z_ctas_per_sm<WARPS>()) zfwd_kernel(SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (threadIdx.x == 0) {
     // its input columns (contiguous, whole 16-byte units) into L2
@@ -31,7 +36,7 @@ __global__ void __launch_bounds__(32 * WARPS, (WARPS <= 8 ? 2 : 1)) zfwd_kernel(
 }
 
 template <typename T, int NZ, int WARPS, bool CONJ, bool H16>
-__global__ void __launch_bounds__(32 * WARPS, (WARPS <= 8 ? 2 : 1)) zinv_kernel(SolveArgs<T> a) {
+__global__ void __launch_bounds__(32 * WARPS, z_ctas_per_sm<WARPS>()) zinv_kernel(SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   zinv_tile<T, NZ, WARPS, CONJ, H16>(a, blockIdx.x, smem_raw);
 }
@@ -110,8 +115,10 @@ PP_Z_INST(PP_Z_TYPE, 32, 8)
 PP_Z_INST(PP_Z_TYPE, 64, 8)
 PP_Z_INST(PP_Z_TYPE, 128, 8)
 PP_Z_INST(PP_Z_TYPE, 256, 8)
+PP_Z_INST(PP_Z_TYPE, 512, 4)
 PP_Z_INST(PP_Z_TYPE, 512, 8)
 PP_Z_INST(PP_Z_TYPE, 512, 16)
+PP_Z_INST(PP_Z_TYPE, 1024, 4)
 PP_Z_INST(PP_Z_TYPE, 1024, 8)
 PP_Z_INST(PP_Z_TYPE, 1024, 16)
 
@@ -119,15 +126,18 @@ template <>
 cudaError_t launch_z<PP_Z_TYPE>(bool forward, int warps, int pipe, bool conj, const SolveArgs<PP_Z_TYPE>& a,
                                 cudaStream_t st) {
   using T = PP_Z_TYPE;
-  const bool w16 = (warps == 16);
+  // 4 and 16 warps per CTA where a column fills a warp (nz >= 512), else 8
+  const bool w16 = (warps == 16), w4 = (warps == 4);
   switch (a.nz) {
     case 32: return zlaunch2<T, 32, 8>(forward, pipe, conj, a, st);
     case 64: return zlaunch2<T, 64, 8>(forward, pipe, conj, a, st);
     case 128: return zlaunch2<T, 128, 8>(forward, pipe, conj, a, st);
     case 256: return zlaunch2<T, 256, 8>(forward, pipe, conj, a, st);
     case 512: return w16 ? zlaunch2<T, 512, 16>(forward, pipe, conj, a, st)
+                    : w4 ? zlaunch2<T, 512, 4>(forward, pipe, conj, a, st)
                          : zlaunch2<T, 512, 8>(forward, pipe, conj, a, st);
     case 1024: return w16 ? zlaunch2<T, 1024, 16>(forward, pipe, conj, a, st)
+                     : w4 ? zlaunch2<T, 1024, 4>(forward, pipe, conj, a, st)
                           : zlaunch2<T, 1024, 8>(forward, pipe, conj, a, st);
     default: return cudaErrorInvalidValue;
   }

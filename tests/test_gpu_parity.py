@@ -118,6 +118,47 @@ def test_stage_z_inverse(nz, dtype, tol):
         assert rel(host(phi), want) < tol
 
 
+def _z_fits(nz, warps, cbytes, pipe):
+    """Shared memory of the z kernels within the 227 KB a CTA can have:
+    single-tile, the FFT scratch or the staging tile (they share it);
+    pipelined, two input or staging tiles plus the FFT scratch."""
+    L = nz // 2
+    g = 4 if L <= 32 else 8 if L <= 128 else 16 if L <= 512 else 32
+    e = L // g
+    cols = warps * (32 // (2 * g))
+    scr = (32 * warps // g) * (e * (g + 1) + 8)
+    stg = cols * (nz + (2 if cbytes == 8 else 1))
+    inw = cols * (nz // 2)
+    need = max(2 * inw + scr + stg, 2 * stg + scr) if pipe else max(scr, stg)
+    return cbytes * need <= 227 * 1024
+
+
+@pytest.mark.parametrize("zw,zp", [(4, 0), (4, 1), (8, 0), (16, 0), (16, 1), (8, 1)])
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 2e-6)])
+@pytest.mark.parametrize("nz", [512, 1024])
+def test_stage_z_cta_sizes(nz, dtype, tol, zw, zp):
+    """Every z CTA size (4, 8, 16 warps) and both tile schedules, forward and
+    inverse, against numpy's real FFTs."""
+    if not _z_fits(nz, zw, 16 if dtype == torch.float64 else 8, zp):
+        pytest.skip("this CTA size does not fit in shared memory at this size")
+    geom, grid = cell_centred(1.0, 1.0, 16, 16, nz, 0.1, modes=4)
+    s = solver(geom, grid, 1, dtype)
+    p = s.plan
+    s.set_plan(z_warps=zw, z_pipe=zp, t_h=p["t_h"], t_threads=p["t_threads"], t_kind=p["t_kind"])
+    rho = random_density(grid.shape, nz + zw)
+    padded = np.concatenate([rho, np.zeros_like(rho)], axis=2)
+    spec_np = np.fft.rfft(padded, axis=2).transpose(2, 0, 1)
+    cdt = torch.complex128 if dtype == torch.float64 else torch.complex64
+    for adj in (0, 1):
+        spec = s.spectrum_buffer()
+        s.stage_z_forward(dev(rho, dtype), spec, adjoint=adj)
+        want = np.conj(spec_np) if adj else spec_np
+        assert rel(spec.cpu().numpy(), want) < tol
+        phi = s.empty()
+        s.stage_z_inverse(torch.tensor(np.ascontiguousarray(want), dtype=cdt, device="cuda"), phi, adjoint=adj)
+        assert rel(host(phi), rho * (2 * nz)) < tol
+
+
 def _transverse_reference(P, geom, grid, igf, adjoint):
     """Per kz plane: padded 2-D DFT, the four-term product with the oracle's
     transformed tables (each F^fff of its own table), unnormalised inverse, crop."""
