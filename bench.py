@@ -248,7 +248,7 @@ def bench_batched(args, count=96):
     import torch
 
     from inputs import bunches
-    from paper_1111_4971_gb300 import PipeSolver, batch_plan_info, batch_status, solve_batched
+    from paper_1111_4971_gb300 import PipeSolver, batch_plan_info, batch_side_streams, batch_status, solve_batched
     items = bunches.workload_batched_96(count=count)
     solvers, rhos = [], []
     for it in items:
@@ -289,7 +289,8 @@ def bench_batched(args, count=96):
             "loop_solves_per_s": count / (loop_ms * 1e-3), "speedup": loop_ms / batch_ms,
             "status_ok": ok, "persistent_solves": persistent,
             "order": ["stage-major", "pipelined", "L2-local"][order],
-            "launches_per_batch": (1 if persistent else 0) + 3 * (count - persistent)}
+            "launches_per_batch": (1 if persistent else 0) + 3 * (count - persistent),
+            "side_streams": batch_side_streams(solvers)}
 
 
 def bench_banded(args):

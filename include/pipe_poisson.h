@@ -214,6 +214,19 @@ int pipe_batch_status(pipe_handle* const* handles, int n);
  * PIPE_EINVAL (null pointers, or no tuned plan for this set). */
 int pipe_batch_plan_info(pipe_handle* const* handles, int n, int* persistent, int* order);
 
+/* The number of side streams (0, 2 or 3) that the first batched call chose
+ * for this exact handle set's single-solve launches: 0 runs them in order on
+ * the caller's stream; otherwise they are dealt round-robin to side streams
+ * that start after the persistent launch and rejoin the caller's stream
+ * through events, so that the solves overlap (parallel branches when the call
+ * is captured in a CUDA graph).  Not in the paper: a GB300 scheduling choice.
+ * Errors: PIPE_EINVAL (null pointers, or no tuned plan for this set). */
+int pipe_batch_side_streams(pipe_handle* const* handles, int n, int* nside);
+/* Override that choice (nside 0, 2 or 3) for the later calls with this set,
+ * for tests and experiments.  Errors: PIPE_EINVAL (other values, null
+ * pointers, or no tuned plan for this set). */
+int pipe_batch_select_streams(pipe_handle* const* handles, int n, int nside);
+
 /* Override that choice for later calls with this exact handle set: `variant`
  * k runs persistent the solves whose z spectrum is smaller than the k-th
  * largest distinct spectrum size of the set (k = 0: every solve), `order` as

@@ -19,7 +19,8 @@ from . import _lib
 from ._lib import PipeError, PipeGeometry, PipeGrid, check
 
 __all__ = ["PipeSolver", "PipePoissonFunction", "CICDeposit", "solve_batched", "batch_status",
-           "batch_inject_fault", "batch_plan_info", "batch_select", "PipeError", "field_energy"]
+           "batch_inject_fault", "batch_plan_info", "batch_select", "batch_side_streams",
+           "batch_select_streams", "PipeError", "field_energy"]
 
 
 def _stream_ptr(stream):
@@ -262,6 +263,24 @@ def batch_status(solvers):
     n = len(solvers)
     hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
     return lib.pipe_batch_status(hs, n)
+
+
+def batch_side_streams(solvers):
+    """Side streams (0, 2 or 3) the tuned plan deals the single-solve launches to."""
+    lib = _lib.load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    k = ctypes.c_int(0)
+    check(lib.pipe_batch_side_streams(hs, n, ctypes.byref(k)), "pipe_batch_side_streams")
+    return k.value
+
+
+def batch_select_streams(solvers, nside):
+    """Override the tuned number of side streams (0, 2 or 3) for this set."""
+    lib = _lib.load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    check(lib.pipe_batch_select_streams(hs, n, int(nside)), "pipe_batch_select_streams")
 
 
 def batch_plan_info(solvers):

@@ -268,7 +268,26 @@ struct BatchPlan {
   bool tuned = false;
   int drop_stage = -1;          // fault injection for the next launch only
   long long spin_limit = 1ll << 22;
+  // the outside solves on nside (2 or 3) side streams, forked from and joined
+  // back to the caller's stream by events (parallel branches when captured in
+  // a graph); nside = 0 runs them in order on the caller's stream
+  static constexpr int kSide = 3;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kSide] = {};
+  int nside = 0;
 };
+
+// the side streams and their events, created on first use
+int side_streams(BatchPlan* b) {
+  if (b->fork) return PIPE_OK;
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return PIPE_ECUDA;
+  for (int i = 0; i < BatchPlan::kSide; ++i) {
+    if (cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) != cudaSuccess) return PIPE_ECUDA;
+    if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess) return PIPE_ECUDA;
+  }
+  return PIPE_OK;
+}
 
 void variant_release(BatchVariant& v) {
   cudaFree(v.solves);
@@ -283,6 +302,11 @@ void batch_release(pipe_handle* h) {
   if (!h || !h->batch) return;
   BatchPlan* b = static_cast<BatchPlan*>(h->batch);
   for (int k = 0; k < BatchPlan::kMaxVar; ++k) variant_release(b->var[k]);
+  for (int i = 0; i < BatchPlan::kSide; ++i) {
+    if (b->side[i]) cudaStreamDestroy(b->side[i]);
+    if (b->join[i]) cudaEventDestroy(b->join[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   delete b;
   h->batch = nullptr;
 }
@@ -486,15 +510,33 @@ static int build_plan(pipe_handle* const* hs, int n, BatchPlan* b) {
 }
 
 // one batched call with variant v: the persistent launch, then the solves
-// outside it, all on stream st
-static int run_variant(BatchPlan* b, int v, pipe_handle* const* hs, const void* const* rho,
+// outside it, in order on stream st (nside = 0) or dealt round-robin to the
+// side streams, which start after the persistent launch and rejoin st
+static int run_variant(BatchPlan* b, int v, int nside, pipe_handle* const* hs, const void* const* rho,
                        void* const* phi, cudaStream_t st) {
   BatchVariant& x = b->var[v];
   int r = b->dtype == PIPE_F64 ? launch_variant<double>(&x, rho, phi, b->drop_stage, b->spin_limit, st)
                                : launch_variant<float>(&x, rho, phi, b->drop_stage, b->spin_limit, st);
+  if (r != PIPE_OK || x.outside.empty()) return r;
+  if (nside == 0) {
+    for (size_t k = 0; r == PIPE_OK && k < x.outside.size(); ++k) {
+      const int s = x.outside[k];
+      r = handle_solve(hs[s], rho[s], phi[s], false, st);
+    }
+    return r;
+  }
+  if ((r = side_streams(b)) != PIPE_OK) return r;
+  if (cudaEventRecord(b->fork, st) != cudaSuccess) return PIPE_ECUDA;
+  for (int i = 0; i < nside; ++i)
+    if (cudaStreamWaitEvent(b->side[i], b->fork, 0) != cudaSuccess) return PIPE_ECUDA;
   for (size_t k = 0; r == PIPE_OK && k < x.outside.size(); ++k) {
     const int s = x.outside[k];
-    r = handle_solve(hs[s], rho[s], phi[s], false, st);
+    r = handle_solve(hs[s], rho[s], phi[s], false, b->side[k % nside]);
+  }
+  // rejoin even after an error, so that a capture is never left unjoined
+  for (int i = 0; i < nside; ++i) {
+    if (cudaEventRecord(b->join[i], b->side[i]) != cudaSuccess) return PIPE_ECUDA;
+    if (cudaStreamWaitEvent(st, b->join[i], 0) != cudaSuccess) return PIPE_ECUDA;
   }
   return r;
 }
@@ -543,22 +585,25 @@ extern "C" int pipe_poisson_solve_batched(pipe_handle* const* handles, const voi
       // time every (variant, work-list order) once after a warm-up run and
       // keep the fastest; these runs are valid solves
       float best = 1e30f;
-      int pick_v = 0, pick_o = 0;
+      int pick_v = 0, pick_o = 0, pick_s = 0;
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       for (int v = 0; v < b->nvar && st == PIPE_OK; ++v)
-        for (int k = 0; k < (b->var[v].n > 0 ? 3 : 1) && st == PIPE_OK; ++k) {
-          b->var[v].items = b->var[v].lists[k];
-          st = run_variant(b, v, handles, rho, phi, s);
-          cudaEventRecord(e0, s);
-          if (st == PIPE_OK) st = run_variant(b, v, handles, rho, phi, s);
-          cudaEventRecord(e1, s);
-          cudaEventSynchronize(e1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (st == PIPE_OK && ms < best) { best = ms; pick_v = v; pick_o = k; }
-        }
+        for (int k = 0; k < (b->var[v].n > 0 ? 3 : 1) && st == PIPE_OK; ++k)
+          for (int ns : {0, 2, 3}) {
+            if (ns > 0 && b->var[v].outside.size() < size_t(ns)) continue;
+            if (st != PIPE_OK) break;
+            b->var[v].items = b->var[v].lists[k];
+            st = run_variant(b, v, ns, handles, rho, phi, s);
+            cudaEventRecord(e0, s);
+            if (st == PIPE_OK) st = run_variant(b, v, ns, handles, rho, phi, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == PIPE_OK && ms < best) { best = ms; pick_v = v; pick_o = k; pick_s = ns; }
+          }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       for (int v = 0; v < b->nvar; ++v) {
@@ -566,11 +611,12 @@ extern "C" int pipe_poisson_solve_batched(pipe_handle* const* handles, const voi
         b->var[v].items = b->var[v].lists[b->var[v].order];
       }
       b->chosen = pick_v;
+      b->nside = pick_s;
       b->tuned = true;
     }
     // an injected fault is meant for the persistent launch: run every solve there
     const int v = b->drop_stage >= 0 ? 0 : b->chosen;
-    if (st == PIPE_OK) st = run_variant(b, v, handles, rho, phi, s);
+    if (st == PIPE_OK) st = run_variant(b, v, b->nside, handles, rho, phi, s);
     b->last = v;
     b->drop_stage = -1;
     b->spin_limit = 1ll << 22;
@@ -612,6 +658,26 @@ extern "C" int pipe_batch_plan_info(pipe_handle* const* handles, int n, int* per
     if (b->handles[s] != handles[s]) return PIPE_EINVAL;
   *persistent = b->var[b->chosen].n;
   *order = b->var[b->chosen].order;
+  return PIPE_OK;
+}
+
+extern "C" int pipe_batch_side_streams(pipe_handle* const* handles, int n, int* nside) {
+  if (!handles || n < 1 || !handles[0] || !nside) return PIPE_EINVAL;
+  BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
+  if (!b || b->n != n || !b->tuned) return PIPE_EINVAL;
+  for (int s = 0; s < n; ++s)
+    if (b->handles[s] != handles[s]) return PIPE_EINVAL;
+  *nside = b->nside;
+  return PIPE_OK;
+}
+
+extern "C" int pipe_batch_select_streams(pipe_handle* const* handles, int n, int nside) {
+  if (!handles || n < 1 || !handles[0] || (nside != 0 && nside != 2 && nside != 3)) return PIPE_EINVAL;
+  BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
+  if (!b || b->n != n || !b->tuned) return PIPE_EINVAL;
+  for (int s = 0; s < n; ++s)
+    if (b->handles[s] != handles[s]) return PIPE_EINVAL;
+  b->nside = nside;
   return PIPE_OK;
 }
 

@@ -34,14 +34,16 @@ def make_set(count, seed=4, dtype=torch.float32):
 
 
 def test_batched_equals_loop_bitwise_and_oracle():
-    from paper_1111_4971_gb300 import batch_plan_info, batch_select, batch_status, solve_batched
+    from paper_1111_4971_gb300 import (batch_plan_info, batch_select, batch_side_streams, batch_status,
+                                       solve_batched)
     items, solvers, rhos = make_set(10)
     phis_b = [s.empty() for s in solvers]
-    solve_batched(solvers, rhos, phis_b)          # tunes the split and the order
+    solve_batched(solvers, rhos, phis_b)          # tunes the split, the order and the side streams
     torch.cuda.synchronize()
     assert batch_status(solvers) == 0
     k, order = batch_plan_info(solvers)
     assert 0 <= k <= 10 and order in (0, 1, 2)
+    assert batch_side_streams(solvers) in (0, 2, 3)
     loop = []
     for s, r, pb in zip(solvers, rhos, phis_b):
         loop.append(s.solve(r))
@@ -115,6 +117,47 @@ def test_batched_graph_replay():
         assert batch_status(solvers) == 0
         for a, b in zip(phis, ref):
             assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("nside", [0, 2, 3])
+def test_batched_side_streams_equal_loop_bitwise(nside):
+    """Every solve outside the persistent launch, dealt to 0, 2 or 3 side
+    streams: the same bits as single solves, eagerly and in a captured graph
+    (where the side streams become parallel branches)."""
+    from paper_1111_4971_gb300 import (PipeSolver, batch_plan_info, batch_select, batch_select_streams,
+                                       batch_status, solve_batched)
+    solvers, rhos = [], []
+    for k in range(6):
+        geom, grid = cell_centred(1.0 + 0.3 * k, 1.0, 32 if k % 2 else 64, 32 if k % 2 else 64,
+                                  64 if k % 2 else 128, 0.05)
+        s = PipeSolver(geom, grid, igf=True, dtype=torch.float32)
+        solvers.append(s)
+        rhos.append(torch.tensor(random_density(grid.shape, 50 + k), dtype=torch.float32, device="cuda"))
+    phis = [s.empty() for s in solvers]
+    solve_batched(solvers, rhos, phis)            # tunes
+    torch.cuda.synchronize()
+    loop = [s.solve(r) for s, r in zip(solvers, rhos)]
+    torch.cuda.synchronize()
+    batch_select(solvers, 2, 0)                   # both size classes outside
+    assert batch_plan_info(solvers)[0] == 0
+    batch_select_streams(solvers, nside)
+    phis = [s.empty().fill_(7.0) for s in solvers]
+    solve_batched(solvers, rhos, phis)
+    torch.cuda.synchronize()
+    assert batch_status(solvers) == 0
+    for a, b in zip(loop, phis):
+        assert torch.equal(a, b)
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            solve_batched(solvers, rhos, phis, stream=stream)
+    for p in phis:
+        p.fill_(7.0)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(loop, phis):
+        assert torch.equal(a, b)
 
 
 def test_batched_wait_timeout_is_reported_and_recovers():

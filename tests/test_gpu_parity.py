@@ -329,3 +329,8 @@ def test_full_size_128x128x1024_sampled_against_direct_sum():
     got = np.array([p64[n] for n in nodes])
     scale = np.abs(p64).max()
     assert np.abs(got - want).max() <= 1e-12 * scale
+    # the FP32 path in the launch configuration the bench times (staged
+    # transverse kernel, 4-warp z CTAs) at the same nodes
+    assert s32.plan["t_kind"] == 2 and s32.plan["z_warps"] == 4
+    got32 = np.array([p32[n] for n in nodes])
+    assert np.abs(got32 - want).max() <= F32_TOL * scale
