@@ -61,6 +61,7 @@ pp::SolveArgs<float> noalloc_args<float>(pipe_handle* h, const void* rho, void* 
   a.tw_t2c = h->tw_t2c_32;
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  a.err = h->err;                      // the handle's error word (set up with it)
   return a;
 }
 template <>
@@ -73,6 +74,7 @@ pp::SolveArgs<double> noalloc_args<double>(pipe_handle* h, const void* rho, void
   a.tbuf = static_cast<double2*>(h->tbuf);
   a.nx = h->grid.nx; a.ny = h->grid.ny; a.nz = h->grid.nz;
   a.sx = h->sx; a.sy = h->sy; a.images = h->images;
+  a.err = h->err;                      // the handle's error word (set up with it)
   return a;
 }
 
