@@ -92,6 +92,21 @@ def test_null_handle_and_pointers(L):
     L.pipe_green_destroy(None)
 
 
+def test_status_fault_hook_and_batch_stream_entry_points_refuse_bad_arguments(L):
+    """Argument checks that come before any CUDA call (no device needed)."""
+    import ctypes
+    assert L.pipe_status(None) == _lib.PIPE_EINVAL
+    assert L.pipe_inject_stage_fault(None, 0, 100) == _lib.PIPE_EINVAL
+    n = ctypes.c_int(-1)
+    assert L.pipe_batch_side_streams(None, 1, ctypes.byref(n)) == _lib.PIPE_EINVAL
+    assert n.value == -1
+    assert L.pipe_batch_select_streams(None, 1, 2) == _lib.PIPE_EINVAL
+    hs = (ctypes.c_void_p * 1)(None)
+    assert L.pipe_batch_side_streams(hs, 1, None) == _lib.PIPE_EINVAL
+    assert L.pipe_batch_select_streams(hs, 1, 2) == _lib.PIPE_EINVAL       # null handle
+    assert L.pipe_batch_select_streams(hs, 0, 2) == _lib.PIPE_EINVAL       # empty set
+
+
 def test_banded_setup_validation_without_gpu(L):
     G, P = _lib.PipeGeometry, _lib.PipeGrid
     cc = G(1.0, 1.0, 0.5 / 128, 0.5 / 128, 20, 20)
