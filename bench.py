@@ -477,6 +477,9 @@ def run_ours(args):
                        "neighbouring steps overlapped with the compute)",
                 "serial_one_call_per_step": serial_value},
         "wall_s_timed_loop": t_wall,
+        # the handle's device error word after the timed steps (0: no bounded
+        # wait of the staged transverse kernel gave up)
+        "device_status": s32.status(),
     }
 
     # ---- FP64 path, free-space (Hockney) comparison, accuracy -------------
