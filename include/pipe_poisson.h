@@ -44,7 +44,7 @@ extern "C" {
 #define PIPE_OK           0
 #define PIPE_EINVAL       1  /* bad argument: sizes, spacings, geometry, null or misaligned pointer */
 #define PIPE_ENOMEM       2  /* device or host allocation failed */
-#define PIPE_EUNSUPPORTED 3  /* valid request outside what this build implements */
+#define PIPE_EUNSUPPORTED 3  /* valid request outside what this library implements */
 #define PIPE_ECUDA        4  /* a CUDA call or kernel launch failed */
 #define PIPE_ETIMEOUT     5  /* a bounded device-side wait gave up (batched launch) */
 #define PIPE_ENODEVICE    6  /* no CUDA device / driver available */
@@ -90,7 +90,7 @@ typedef struct pipe_handle pipe_handle;
  * on the doubled grid and transform it (Sec. 2, after Eq. 10; Sec. 5: computed
  * once, stored, reused).  Allocates every device buffer the solves need.
  *
- * Supported in this build: nx == ny in {16, 32, 64, 128}; nz in
+ * Supported by this library: nx == ny in {16, 32, 64, 128}; nz in
  * {32, 64, 128, 256, 512, 1024}; 1 <= modes <= 4096.  Meshes that span the
  * pipe (nx*hx == a, ny*hy == b to 1e-12 relative) with 2*x0/hx and 2*y0/hy
  * integers (cell-centred x0 = hx/2, or a node on the wall x0 = 0) store one
