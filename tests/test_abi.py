@@ -122,3 +122,22 @@ def test_banded_setup_validation_without_gpu(L):
         st = L.pipe_banded_setup(ctypes.byref(geo), ctypes.byref(grid), 1, n_nb, ctypes.byref(h))
         assert st == want, (n_nb, st)
         assert not h.value
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: loading a library that is not there raises, in a
+    fresh interpreter (the module caches the loaded library)."""
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_1111_4971_gb300 import _lib\n"
+        "try:\n"
+        "    _lib.load(%r)\n"
+        "except RuntimeError as e:\n"
+        "    print('raised', 'no fallback' in str(e))\n"
+        "else:\n"
+        "    print('loaded')\n"
+    ) % (str(__import__('pathlib').Path(__file__).resolve().parents[1]), str(tmp_path / "absent.so"))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert out.stdout.strip() == "raised True", out.stdout + out.stderr
