@@ -576,6 +576,8 @@ extern "C" int pipe_poisson_solve_batched(pipe_handle* const* handles, const voi
       for (int s = 0; s < n; ++s) b->handles[s] = handles[s];
       handles[0]->batch = b;
       st = b->dtype == PIPE_F64 ? build_plan<double>(handles, n, b) : build_plan<float>(handles, n, b);
+      // the side streams exist before any later call can be captured
+      if (st == PIPE_OK) st = side_streams(b);
       if (st != PIPE_OK) batch_release(handles[0]);
     }
   }
