@@ -46,7 +46,7 @@ extern "C" {
 #define PIPE_ENOMEM       2  /* device or host allocation failed */
 #define PIPE_EUNSUPPORTED 3  /* valid request outside what this library implements */
 #define PIPE_ECUDA        4  /* a CUDA call or kernel launch failed */
-#define PIPE_ETIMEOUT     5  /* a bounded device-side wait gave up (batched launch) */
+#define PIPE_ETIMEOUT     5  /* a bounded device-side wait gave up (batched launch, staged transverse kernel) */
 #define PIPE_ENODEVICE    6  /* no CUDA device / driver available */
 
 /* dtypes */
@@ -57,8 +57,9 @@ extern "C" {
  * per z-transform tile of columns after the forward z transform, one per
  * transverse row after the transverse stage; the Green product is taken in
  * FP16 on operands scaled per transverse column.  An optional variant whose
- * error (about 1e-3 relative, FP16 rounding 2^-11) is above the FP32 path's
- * 1e-5: for uses whose error budget allows it.  Cell-centred meshes only;
+ * error (1e-4 to 4e-4 relative against the FP64 solve, below 8 FP16 rounding
+ * units 2^-11) is above the FP32 path's 1e-5: for uses whose error budget
+ * allows it.  Cell-centred meshes only;
  * solves, adjoints and host solves; not the stage, no-alloc, batched or
  * banded entry points (PIPE_EUNSUPPORTED).  Fields are FP32 tensors. */
 #define PIPE_F32_C16 2
@@ -90,14 +91,33 @@ typedef struct pipe_handle pipe_handle;
  * on the doubled grid and transform it (Sec. 2, after Eq. 10; Sec. 5: computed
  * once, stored, reused).  Allocates every device buffer the solves need.
  *
- * Supported by this library: nx == ny in {16, 32, 64, 128}; nz in
- * {32, 64, 128, 256, 512, 1024}; 1 <= modes <= 4096.  Meshes that span the
- * pipe (nx*hx == a, ny*hy == b to 1e-12 relative) with 2*x0/hx and 2*y0/hy
- * integers (cell-centred x0 = hx/2, or a node on the wall x0 = 0) store one
- * real octant of the spectrum; any other mesh inside the pipe (a transverse
- * window, Sec. 5: smaller than the cross-section, at any origin) uses the
- * general form of Eq. 10 with the four transformed tables stored in full,
- * for nx == ny <= 64.
+ * Two forms of the same operator, chosen per handle (pipe_get_plan's t_kind
+ * reports which; pipe_set_plan and pipe_autotune can change it):
+ *  - the padded transforms of Eq. 10: nx == ny in {16, 32, 64, 128}; nz in
+ *    {32, 64, 128, 256, 512, 1024}; 1 <= modes <= 4096.  Meshes that span
+ *    the pipe (nx*hx == a, ny*hy == b to 1e-12 relative) with 2*x0/hx and
+ *    2*y0/hy integers (cell-centred x0 = hx/2, or a node on the wall x0 = 0)
+ *    store one real octant of the spectrum; any other mesh inside the pipe
+ *    (a transverse window, Sec. 5: smaller than the cross-section, at any
+ *    origin) uses the general form of Eq. 10 with the four transformed
+ *    tables stored in full, for nx == ny <= 64.
+ *  - the mode-space form (t_kind 3): the same sum with the transverse
+ *    transforms pruned to the modes of the truncated series (Eq. 7), where
+ *    the transformed Green function is nonzero: a projection of rho onto the
+ *    modes_m x modes_n sine modes, the zero-padded z convolution of each
+ *    mode's column by FFT (Appendix A), and the back-projection.  Any mesh
+ *    inside the pipe with nx and ny multiples of 16 (nx != ny allowed, up to
+ *    4096 each), nz in {32, ..., 1024} as above, modes_m, modes_n <= 32;
+ *    PIPE_F32 or PIPE_F64; not banded; and its kernels' shared memory within
+ *    the device's 227 KB per CTA (it grows with ny and the modes: FP32 with
+ *    20 x 20 modes takes ny up to about 1400, FP64 about 700).  Its tables
+ *    (FP64, with FP32 copies) take (nx*mxp + ny*myp + mxp*myp*(nz+1))*12
+ *    bytes and its scratch (xblocks + 1)*mxp*myp*nz values of the dtype (the
+ *    sizes of pipe_mode_layout).
+ *    The default where the modes are at most half the transverse mesh
+ *    (2*max(ceil4(modes_m), slots) <= min(nx, ny)) or the padded transforms
+ *    cannot take the mesh.
+ * A mesh that neither form takes gives PIPE_EUNSUPPORTED.
  * Errors: PIPE_EINVAL (non-positive sizes or spacings, mesh not inside the
  * pipe, bad dtype / igf, out == NULL), PIPE_EUNSUPPORTED (other sizes or
  * meshes), PIPE_ENOMEM, PIPE_ECUDA.  On error *out is set to NULL.
@@ -145,22 +165,34 @@ int pipe_poisson_solve(pipe_handle* h, const void* rho, void* phi, void* stream)
 int pipe_poisson_adjoint(pipe_handle* h, const void* dphi, void* drho, void* stream);
 
 /* pipe_poisson_solve without any device allocation by the library: the
- * solve's working buffer (the z half-spectrum, (nz+1)*nx*ny complex values of
- * the handle's dtype) is a fixed 64 MiB device array that belongs to the
- * library and stays reserved on every GPU that loads it until the process
- * exits.  Meant for programs that must not let a library allocate device
- * memory while they run (a host that keeps the GPU's memory in its own pool,
- * a loop that cannot risk an allocation stalling or failing): they create the
- * handle during initialisation and call this afterwards.  The paper has no
- * counterpart; it is an interface convenience.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current).  All calls share the array: calls whose
- * kernels overlap on the GPU (other streams or handles at the same time) race
- * and corrupt each other's results.  Nothing needs clearing between calls.
- * Same arguments as pipe_poisson_solve.  Errors: PIPE_EINVAL (null or
- * misaligned pointers), PIPE_EUNSUPPORTED when (nz+1)*nx*ny complex values of
- * the dtype exceed 64 MiB (e.g. 128x128x256 FP32 fits, 128x128x512 FP32 does
- * not), PIPE_ECUDA. */
+ * solve's working buffer is a fixed 64 MiB device array that belongs to the
+ * library instead of device memory owned by the handle -- for the
+ * padded-transform form the z half-spectrum, (nz+1)*nx*ny complex values of
+ * the dtype; for the mode-space form (plan t_kind 3) the projections and the
+ * convolved mode columns, (xblocks+1)*mxp*myp*nz values (pipe_mode_layout).
+ * The handle's current form runs, so the result is bit for bit that of
+ * pipe_poisson_solve.  Meant for programs that must not let a library
+ * allocate device memory while they run (a host that keeps the GPU's memory
+ * in its own pool, a loop that cannot risk an allocation stalling or
+ * failing): they create the handle during initialisation and call this
+ * afterwards.  The paper has no counterpart; it is an interface convenience.
+ * The array is reserved on a device when a handle is set up there (the setup
+ * looks up its device address, with that device current; a failure there is
+ * reported by the first call of this entry point, which tries again), and it
+ * stays reserved until the process exits.  The first launch of each kernel
+ * on a device also loads that kernel's code (the CUDA runtime's lazy
+ * loading): a program that must not see that memory taken later makes one
+ * call during initialisation or sets CUDA_MODULE_LOADING=EAGER.  After
+ * cudaDeviceReset every handle on that device is invalid; a handle set up
+ * afterwards looks the address up again.  All calls share the array: calls
+ * whose kernels overlap on the GPU (other streams or handles at the same
+ * time) race and corrupt each other's results.  Nothing needs clearing
+ * between calls.  Same arguments as pipe_poisson_solve.  Errors: PIPE_EINVAL
+ * (null or misaligned pointers), PIPE_EUNSUPPORTED when the buffer exceeds
+ * 64 MiB (e.g. 128x128x256 FP32 in the transform form fits, 128x128x512 does
+ * not; the mode-space form of 128x128x1024 FP32 with 20 x 20 modes takes
+ * 3.3 MB), or for banded, complex-FP16 or window (transform form) handles,
+ * PIPE_ECUDA. */
 int pipe_poisson_solve_noalloc(pipe_handle* h, const void* rho, void* phi, void* stream);
 
 /* Same as pipe_poisson_solve but rho_host / phi_host are HOST arrays: the
@@ -266,6 +298,48 @@ int pipe_green_spectrum(pipe_handle* h, double* out, size_t count);
 int pipe_stage_z_forward(pipe_handle* h, const void* rho, void* spec, int adjoint, void* stream);
 int pipe_stage_transverse(pipe_handle* h, void* spec, int adjoint, void* stream);
 int pipe_stage_z_inverse(pipe_handle* h, const void* spec, void* phi, int adjoint, void* stream);
+/* (The three stages above exist on handles of the padded-transform form;
+ * PIPE_EUNSUPPORTED on a handle that only the mode-space form takes.) */
+
+/* Layout of the mode-space form (Sec. 2 Eq. 7: the sine modes of the
+ * truncated series).  mx = modes_m; mxp = mx rounded up to a multiple of 4;
+ * myp = the y-mode slots: when the mesh is symmetric about the pipe's
+ * mid-plane in y (2*y0 + (ny-1)*hy == b, e.g. cell-centred), *fold = 1 and
+ * slot s < myp/2 holds mode n = 2s+1, slot s >= myp/2 mode n = 2(s - myp/2)+2;
+ * otherwise *fold = 0 and slot s holds n = s+1 (slots beyond modes_n are
+ * zero).  Mode column c = (m-1)*myp + slot.  xblocks: the groups of x rows
+ * whose projections the first stage writes separately (the kernel works on
+ * blocks of 16 rows in FP32, 8 in FP64, and sums up to 8 neighbouring blocks
+ * in a thread-block cluster; xblocks = blocks / that cluster size, 1 for
+ * FP32 nx = 128).  Errors: PIPE_EINVAL (null pointers), PIPE_EUNSUPPORTED
+ * (the mode-space form cannot take the handle). */
+int pipe_mode_layout(pipe_handle* h, int* mx, int* mxp, int* myp, int* fold, int* xblocks);
+
+/* The FP64 kernel spectra of the mode-space form, [c][kz] for the mxp*myp
+ * mode columns and kz = 0..nz: the DCT-I of the doubled z table of
+ *     K_mn(d) = hx*hy*hz * (8*pi/(a*b)) * f_mn(d*hz) / kappa_mn
+ * (f = exp(-kappa |w|) of Eq. 9, or the IGF g_z of Eq. 15), with the free
+ * slot d = nz filled by the formula, divided by 2*nz; zero for padded
+ * columns.  count must be mxp*myp*(nz+1).  Synchronous.  For inspection and
+ * tests.  Errors: PIPE_EINVAL, PIPE_EUNSUPPORTED as pipe_mode_layout. */
+int pipe_mode_spectrum(pipe_handle* h, double* out, size_t count);
+
+/* Stages of the mode-space form, for inspection and per-kernel tests (device
+ * arrays of the handle's dtype, caller-owned, 16-byte aligned; asynchronous):
+ *   stage 0: in = rho [nx][ny][nz] -> out = part [xblocks][mxp*myp][nz], the
+ *            projection of each block of x rows (block b: rows b*nx/xblocks ..)
+ *            part[b][c][k] = sum_{i in block b} sum_j sin(m pi x_i/a) *
+ *                            sin(n pi y_j/b) rho[i][j][k]
+ *   stage 1: in = part -> out = psi [mxp*myp][nz]: the blocks summed, each
+ *            column convolved along z with its kernel (zero-padded 2nz-point
+ *            transforms, the spectrum of pipe_mode_spectrum), first nz values
+ *   stage 2: in = psi -> out = phi [nx][ny][nz]:
+ *            phi[i][j][k] = sum_{m,n} sin(m pi x_i/a) sin(n pi y_j/b) psi[c][k]
+ * The three in a row are the solve of this form (pipe_poisson_solve with plan
+ * t_kind 3); it is symmetric, so the adjoint is the same chain.
+ * Errors: PIPE_EINVAL (stage outside 0..2, null or misaligned pointers),
+ * PIPE_EUNSUPPORTED as pipe_mode_layout, PIPE_ECUDA. */
+int pipe_stage_modes(pipe_handle* h, int stage, const void* in, void* out, void* stream);
 
 /* Time the kernel variants available for this handle's sizes on `stream` and
  * keep the fastest (per size and dtype, shared by all handles of that shape in
@@ -289,10 +363,15 @@ int pipe_autotune(pipe_handle* h, void* stream);
  * kz planes) whose input rows arrive by bulk asynchronous copies into shared
  * memory, the next plane's first rows while the current plane is still being
  * transformed; same meshes as 1, plane buffer in shared memory only (not
- * FP64 128^2).  pipe_set_plan returns PIPE_EINVAL for values outside those
- * sets and PIPE_EUNSUPPORTED for t_kind 1 or 2 on other meshes; a variant
- * that does not fit the device (shared memory) makes the next solve fail
- * with PIPE_ECUDA.
+ * FP64 128^2).  t_kind 3 selects the mode-space form of pipe_green_setup
+ * (the other fields then keep the transform plan for a later switch back);
+ * pipe_get_plan reports 3 while it is selected.  pipe_set_plan returns
+ * PIPE_EINVAL for values outside those sets and PIPE_EUNSUPPORTED for t_kind
+ * 1 or 2 on other meshes, for t_kind 3 on a handle the mode-space form cannot
+ * take, and for t_kind 0..2 on a handle only the mode-space form takes; a
+ * variant that does not fit the device (shared memory) makes the next solve
+ * fail with PIPE_ECUDA.  pipe_autotune, on a handle that both forms take,
+ * also times a few solves of each and keeps the faster form.
  * The free-space (Hockney) handle ignores t_kind. */
 int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h, int* t_threads, int* t_kind);
 int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads, int t_kind);

@@ -183,6 +183,35 @@ class PipeSolver:
                                             _stream_ptr(stream)), "pipe_stage_z_inverse")
         return phi
 
+    # -- the mode-space form (plan t_kind 3) -----------------------------
+    def mode_layout(self):
+        """(mx, mxp, myp, fold, xblocks) of the mode-space form (pipe_mode_layout)."""
+        v = [ctypes.c_int() for _ in range(5)]
+        check(self.lib.pipe_mode_layout(self.handle, *[ctypes.byref(x) for x in v]), "pipe_mode_layout")
+        return tuple(x.value for x in v)
+
+    def mode_spectrum(self):
+        """FP64 kernel spectra [mxp*myp, nz+1] of the mode columns (pipe_mode_spectrum)."""
+        import numpy as np
+        _, mxp, myp, _, _ = self.mode_layout()
+        out = np.empty((mxp * myp, self.shape[2] + 1), dtype=np.float64)
+        check(self.lib.pipe_mode_spectrum(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          out.size), "pipe_mode_spectrum")
+        return out
+
+    def mode_buffers(self):
+        """Empty (part, psi) device arrays for the mode-space stages."""
+        _, mxp, myp, _, xb = self.mode_layout()
+        nz = self.shape[2]
+        return (torch.empty((xb, mxp * myp, nz), dtype=self.dtype, device=self.device),
+                torch.empty((mxp * myp, nz), dtype=self.dtype, device=self.device))
+
+    def stage_modes(self, stage: int, inp: torch.Tensor, out: torch.Tensor, stream=None):
+        """One stage of the mode-space form: 0 rho -> part, 1 part -> psi, 2 psi -> phi."""
+        check(self.lib.pipe_stage_modes(self.handle, int(stage), _ptr(inp), _ptr(out), _stream_ptr(stream)),
+              "pipe_stage_modes")
+        return out
+
     def autotune(self, stream=None):
         check(self.lib.pipe_autotune(self.handle, _stream_ptr(stream)), "pipe_autotune")
         return self.plan

@@ -59,6 +59,10 @@ SIGNATURES = {
     "pipe_stage_z_forward": (c_int, [H, c_void_p, c_void_p, c_int, c_void_p]),
     "pipe_stage_transverse": (c_int, [H, c_void_p, c_int, c_void_p]),
     "pipe_stage_z_inverse": (c_int, [H, c_void_p, c_void_p, c_int, c_void_p]),
+    "pipe_stage_modes": (c_int, [H, c_int, c_void_p, c_void_p, c_void_p]),
+    "pipe_mode_layout": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                 POINTER(c_int)]),
+    "pipe_mode_spectrum": (c_int, [H, POINTER(c_double), c_size_t]),
     "pipe_autotune": (c_int, [H, c_void_p]),
     "pipe_get_plan": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
                               POINTER(c_int)]),

@@ -553,7 +553,7 @@ extern "C" int pipe_poisson_solve_batched(pipe_handle* const* handles, const voi
     if (!handles[s] || !rho[s] || !phi[s]) return PIPE_EINVAL;
     if ((reinterpret_cast<uintptr_t>(rho[s]) | reinterpret_cast<uintptr_t>(phi[s])) % 16) return PIPE_EINVAL;
     if (handles[s]->grid.dtype != handles[0]->grid.dtype || handles[s]->device != handles[0]->device ||
-        !handles[s]->images || handles[s]->banded >= 0 || handles[s]->general ||
+        !handles[s]->images || handles[s]->banded >= 0 || handles[s]->general || !handles[s]->fft_ok ||
         handles[s]->grid.dtype == PIPE_F32_C16)
       return PIPE_EUNSUPPORTED;
     for (int r = 0; r < s; ++r)

@@ -412,4 +412,61 @@ done:
   return err;
 }
 
+
+// ---------------------------------------------------------------------------
+// Tables of the mode-space solve (modes_impl.cuh), all FP64 with FP32 copies:
+//   sx[i][s] = sin(m pi x_i / a), m = s + 1 (zero for m > Mx), i < nx, s < mxp
+//   sy[j][s] = sin(n pi y_j / b) for the mode n of slot s (mode_of_slot), j < nyk
+//   gz[c][kz], c = s_x * myp + s_y: the DCT-I of the doubled z table of
+//       K_mn(d) = hx hy hz (8 pi / ab) kappa_mn^{-1} f_mn(d hz)
+//   (f the e^{-kappa |w|} of Eq. 9 or the IGF g_z of Eq. 15), divided by 2nz.
+// ---------------------------------------------------------------------------
+__global__ void mode_sine_kernel(double* t64, float* t32, int rows, int slots, int nmodes, int fold,
+                                 double origin, double h, double len) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * slots) return;
+  const int r = idx / slots, s = idx % slots;
+  const int mode = !fold ? s + 1 : (s < slots / 2 ? 2 * s + 1 : 2 * (s - slots / 2) + 2);
+  const double v = mode <= nmodes ? sinpi(double(mode) * (origin + double(r) * h) / len) : 0.0;
+  t64[idx] = v;
+  t32[idx] = float(v);
+}
+
+__global__ void mode_gz_kernel(double* g64, float* g32, const double* Zh, int M, int N, int mxp, int myp,
+                               int fold, int nz, double C) {
+  const long idx = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= long(mxp) * myp * (nz + 1)) return;
+  const int kz = int(idx % (nz + 1));
+  const int c = int(idx / (nz + 1));
+  const int m = c / myp + 1, s = c % myp;
+  const int n = !fold ? s + 1 : (s < myp / 2 ? 2 * s + 1 : 2 * (s - myp / 2) + 2);
+  const double v = (m <= M && n <= N) ? C * Zh[(long(m - 1) * N + (n - 1)) * (nz + 1) + kz] : 0.0;
+  g64[idx] = v;
+  g32[idx] = float(v);
+}
+
+cudaError_t build_mode_tables(const GreenSpec& s, double x0, double y0, int mxp, int myp, int fold,
+                              double* sx64, float* sx32, double* sy64, float* sy32, double* gz64,
+                              float* gz32, cudaStream_t st) {
+  const int M = s.modes_m, N = s.modes_n, nz = s.nz;
+  const int nyk = fold ? s.ny / 2 : s.ny;
+  double *Z = nullptr, *Zh = nullptr, *cosn = nullptr;
+  cudaError_t err = cudaSuccess;
+  if ((err = cudaMalloc(&Z, sizeof(double) * size_t(M) * N * (nz + 1))) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&Zh, sizeof(double) * size_t(M) * N * (nz + 1))) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&cosn, sizeof(double) * 2 * nz)) != cudaSuccess) goto done;
+  mode_sine_kernel<<<nblk(long(s.nx) * mxp, 256), 256, 0, st>>>(sx64, sx32, s.nx, mxp, M, 0, x0, s.hx, s.a);
+  mode_sine_kernel<<<nblk(long(nyk) * myp, 256), 256, 0, st>>>(sy64, sy32, nyk, myp, N, fold, y0, s.hy, s.b);
+  z_profile_kernel<<<nblk(long(M) * N * (nz + 1), 256), 256, 0, st>>>(Z, M, N, nz, s.hz, s.a, s.b, s.igf);
+  cos_pi_table_kernel<<<nblk(2 * nz, 256), 256, 0, st>>>(cosn, nz);
+  z_dct_kernel<<<nblk(long(M) * N * (nz + 1), 256), 256, 0, st>>>(Zh, Z, M * N, nz, cosn);
+  mode_gz_kernel<<<nblk(long(mxp) * myp * (nz + 1), 256), 256, 0, st>>>(
+      gz64, gz32, Zh, M, N, mxp, myp, fold, nz, s.hx * s.hy * s.hz * 8.0 * M_PI / (s.a * s.b) / (2.0 * nz));
+  if ((err = cudaGetLastError()) != cudaSuccess) goto done;
+  err = cudaStreamSynchronize(st);
+done:
+  cudaFree(Z); cudaFree(Zh); cudaFree(cosn);
+  return err;
+}
+
 }  // namespace pp

@@ -51,14 +51,42 @@ struct pipe_handle {
   cudaEvent_t ev_in[2] = {nullptr, nullptr};
   cudaEvent_t ev_done[2] = {nullptr, nullptr};
   cudaEvent_t ev_out[2] = {nullptr, nullptr};
+  // mode-space solve (modes_impl.cuh): its tables, FP64 and FP32, and its
+  // scratch (the x blocks' projections, then the z-convolved mode columns)
+  int modes_ok = 0;            // the mode path can run this handle
+  int use_modes = 0;           // solves take the mode path (plan t_kind 3)
+  int fft_ok = 1;              // the padded-transform path's buffers exist
+  int mxp = 0, myp = 0, fy = 0;
+  double *msx64 = nullptr, *msy64 = nullptr, *mgz64 = nullptr;
+  float *msx32 = nullptr, *msy32 = nullptr, *mgz32 = nullptr;
+  void* mwork = nullptr;       // part [xblocks][mc][nz], then psi [mc][nz], of the dtype
+  float* msy_host = nullptr;   // FP32 y-mode table in host memory (the projection's kernel parameter)
+  int mfast = 0;               // FP32 projection / back-projection in their occupancy layout
   pp::Plan plan{8, 0, 1, 256};
   pp::Plan free_plan{8, 0, 1, 256};   // transverse shape of the free-space stage
   void* batch = nullptr;       // batched work list owned by this handle
 };
 
 namespace pp {
+template <typename T>
+struct SolveArgs;
+// launch arguments of the padded-transform form with `work` as its working buffer
+template <typename T>
+SolveArgs<T> make_args(pipe_handle* h, const void* rho, void* phi, void* work);
+// that form's three stages (z forward, transverse stage, z inverse) on a's buffers
+template <typename T>
+int transform_chain(pipe_handle* h, const SolveArgs<T>& a, bool adjoint, cudaStream_t st);
+// looks up (again) the device address of the no-alloc solve's fixed array on
+// the current device `dev`; the setups call it so that the array is reserved
+// when a handle is created
+int noalloc_reserve(int dev);
 Plan default_plan(int n, int nz, bool f64, bool cell_centred);   // pipe operator
 Plan default_free_plan(int n, int nz, bool f64);   // free-space stage
 void batch_release(pipe_handle* h);
 int handle_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStream_t st);
+// the mode-space solve with `scratch` (mode_scratch_bytes) as its working buffer
+int mode_solve(pipe_handle* h, const void* rho, void* phi, void* scratch, cudaStream_t st);
+size_t mode_scratch_bytes(const pipe_handle* h);
+// x blocks of the projection (nx / rows per CTA of the dtype)
+int mode_xblocks(const pipe_handle* h);
 }  // namespace pp

@@ -1,0 +1,110 @@
+// Kernels and host launchers of the mode-space solve (the method and the
+// device routines are described in modes_impl.cuh).
+#include "modes.cuh"
+#include "modes_impl.cuh"
+
+namespace pp {
+
+template <typename T, int MYP, bool FY>
+__global__ void __launch_bounds__(128) mode_project_kernel(ModeArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  mode_project<T, MYP, FY>(a, smem_raw);
+}
+
+template <typename T, int MYP, bool FY>
+__global__ void __launch_bounds__(128) mode_back_kernel(ModeArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  mode_back<T, MYP, FY>(a, smem_raw);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) mode_z_kernel(ModeArgs<T> a, int groups) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  mode_z<T>(a, groups, smem_raw);
+}
+
+namespace {
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t smem) {
+  if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+template <typename T, int MYP, bool FY>
+cudaError_t launch_pb(int which, const ModeArgs<T>& a, cudaStream_t st) {
+  using S = ModeShape<T>;
+  const int xblocks = a.nx / S::XB;
+  const dim3 grid(unsigned(a.nz / S::ZC), unsigned(xblocks));
+  cudaError_t e;
+  if (which == 0) {
+    const size_t smem = mode_proj_smem<T>(a.ny, a.mxp, MYP, FY);
+    void (*kern)(ModeArgs<T>) = mode_project_kernel<T, MYP, FY>;
+    if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(S::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = unsigned(mode_cluster(xblocks));
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+  }
+  const size_t smem = mode_back_smem<T>(a.ny, a.mx, a.mxp, MYP, FY);
+  void (*kern)(ModeArgs<T>) = mode_back_kernel<T, MYP, FY>;
+  if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+  kern<<<grid, S::THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int MYP>
+cudaError_t launch_pb2(int which, bool fy, const ModeArgs<T>& a, cudaStream_t st) {
+  return fy ? launch_pb<T, MYP, true>(which, a, st) : launch_pb<T, MYP, false>(which, a, st);
+}
+
+// 256 threads per CTA, L/4 per column (L = nz in 32..1024)
+template <typename T>
+cudaError_t launch_zc(const ModeArgs<T>& a, cudaStream_t st) {
+  const int per = 1024 / a.nz;                       // columns per CTA
+  const size_t smem = sizeof(C2<T>) * (size_t(per) * 2 * a.nz + 3 * size_t(a.nz));
+  void (*kern)(ModeArgs<T>, int) = mode_z_kernel<T>;
+  cudaError_t e;
+  if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+  const int xblocks = a.nx / ModeShape<T>::XB;
+  kern<<<(a.mc + per - 1) / per, 256, smem, st>>>(a, xblocks / mode_cluster(xblocks));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#ifndef PP_M_TYPE
+#define PP_M_TYPE float
+#endif
+
+template <>
+cudaError_t launch_mode_stage<PP_M_TYPE>(int stage, int myp, bool fy, const ModeArgs<PP_M_TYPE>& a,
+                                         cudaStream_t st) {
+  using T = PP_M_TYPE;
+  if (stage == 1) {
+    if (a.nz < 32 || a.nz > 1024 || (a.nz & (a.nz - 1))) return cudaErrorInvalidValue;
+    return launch_zc<T>(a, st);
+  }
+  const int which = stage == 0 ? 0 : 1;
+  switch (myp) {
+    case 8: return launch_pb2<T, 8>(which, fy, a, st);
+    case 12: return launch_pb2<T, 12>(which, fy, a, st);
+    case 16: return launch_pb2<T, 16>(which, fy, a, st);
+    case 20: return launch_pb2<T, 20>(which, fy, a, st);
+    case 24: return launch_pb2<T, 24>(which, fy, a, st);
+    case 32: return launch_pb2<T, 32>(which, fy, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pp

@@ -206,8 +206,50 @@ int tune(pipe_handle* h, cudaStream_t st, Plan* out) {
 
 using namespace pp;
 
+namespace pp {
+namespace {
+// where both forms can run the handle: time a few full solves of each (the
+// transform form with its tuned plan) and keep the faster
+int choose_form(pipe_handle* h, cudaStream_t st) {
+  const size_t n = size_t(h->grid.nx) * h->grid.ny * h->grid.nz * (h->grid.dtype == PIPE_F64 ? 8 : 4);
+  void *rho = nullptr, *phi = nullptr;
+  if (cudaMalloc(&rho, n) != cudaSuccess) return PIPE_ENOMEM;
+  if (cudaMalloc(&phi, n) != cudaSuccess) { cudaFree(rho); return PIPE_ENOMEM; }
+  cudaMemsetAsync(rho, 0, n, st);
+  float ms[2] = {-1.f, -1.f};
+  for (int m = 0; m < 2; ++m) {
+    h->use_modes = m;
+    ms[m] = time_ms([&] { return handle_solve(h, rho, phi, false, st) == PIPE_OK ? cudaSuccess
+                                                                                 : cudaErrorUnknown; },
+                    st, 5);
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(rho);
+  cudaFree(phi);
+  if (ms[0] < 0 && ms[1] < 0) return PIPE_ECUDA;
+  h->use_modes = (ms[1] > 0 && (ms[0] < 0 || ms[1] <= ms[0])) ? 1 : 0;
+  return PIPE_OK;
+}
+}  // namespace
+}  // namespace pp
+
+static int autotune_transforms(pipe_handle* h, void* stream);
+
 extern "C" int pipe_autotune(pipe_handle* h, void* stream) {
   if (!h) return PIPE_EINVAL;
+  if (!h->fft_ok) return PIPE_OK;                        // mode-space form only: nothing to choose
+  const int s = autotune_transforms(h, stream);
+  if (s != PIPE_OK || !h->modes_ok) return s;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) cudaSetDevice(h->device);
+  const int c = choose_form(h, static_cast<cudaStream_t>(stream));
+  if (dev >= 0 && dev != h->device) cudaSetDevice(dev);
+  return c;
+}
+
+// the transform form's plan: per shape, timed once per process (and cached)
+static int autotune_transforms(pipe_handle* h, void* stream) {
   if (h->grid.dtype == PIPE_F32_C16) return PIPE_OK;     // fixed variant: nothing to choose
   // banded handles are keyed by their neighbour count as well
   const Key k(h->grid.nx, h->grid.nz,
@@ -247,15 +289,21 @@ extern "C" int pipe_get_plan(pipe_handle* h, int* z_warps, int* z_pipe, int* t_h
   *z_pipe = h->plan.z_pipe;
   *t_h = p.t_h;
   *t_threads = p.t_threads;
-  *t_kind = p.t_kind;
+  *t_kind = h->use_modes ? 3 : p.t_kind;
   return PIPE_OK;
 }
 
 extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, int t_threads, int t_kind) {
   if (!h) return PIPE_EINVAL;
   if ((z_warps != 4 && z_warps != 8 && z_warps != 16) || (z_pipe != 0 && z_pipe != 1) || (t_h != 1 && t_h != 2 && t_h != 4) ||
-      (t_threads != 128 && t_threads != 256 && t_threads != 512) || t_kind < 0 || t_kind > 2)
+      (t_threads != 128 && t_threads != 256 && t_threads != 512) || t_kind < 0 || t_kind > 3)
     return PIPE_EINVAL;
+  if (t_kind == 3) {                    // the mode-space form; the transform plan is kept
+    if (!h->modes_ok) return PIPE_EUNSUPPORTED;
+    h->use_modes = 1;
+    return PIPE_OK;
+  }
+  if (!h->fft_ok) return PIPE_EUNSUPPORTED;
   if (t_kind >= 1) {
     // the N-point routine: pipe operator on cell-centred meshes, one CTA per
     // plane, the N x N plane buffer in shared memory (kind 1: or in global
@@ -264,6 +312,7 @@ extern "C" int pipe_set_plan(pipe_handle* h, int z_warps, int z_pipe, int t_h, i
     const size_t c = h->grid.dtype == PIPE_F64 ? 16 : 8;
     if (c * h->grid.nx * h->grid.ny > 200 * 1024 && (t_kind == 2 || !h->tbuf)) return PIPE_EUNSUPPORTED;
   }
+  h->use_modes = 0;
   if (h->images) h->plan = Plan{z_warps, z_pipe, t_h, t_threads, t_kind};
   else {
     h->plan.z_warps = z_warps;

@@ -71,12 +71,17 @@ def test_setup_validation_without_gpu(L):
         (good_geo, P(128, 128, 256, 1 / 128, 1 / 128, 0.1, 5), 1, _lib.PIPE_EINVAL),  # dtype
         (G(1.0, 1.0, 0.5, 0.0, 20, 20), good, 1, _lib.PIPE_EINVAL),      # mesh leaves the pipe
         (G(1.0, 1.0, 0.0, 0.0, 0, 20), good, 1, _lib.PIPE_EINVAL),       # no modes
-        (good_geo, P(96, 96, 256, 1 / 96, 1 / 96, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),  # not 2^k
-        (good_geo, P(128, 64, 256, 1 / 128, 1 / 64, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),  # nx != ny
+        # sizes neither form takes: not a power of two nor a multiple of 16
+        (good_geo, P(100, 100, 256, 1 / 100, 1 / 100, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),
+        (good_geo, P(128, 72, 256, 1 / 128, 1 / 72, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),   # nx != ny, 72
         (good_geo, P(128, 128, 4096, 1 / 128, 1 / 128, 0.1, 0), 1, _lib.PIPE_EUNSUPPORTED),
-        (G(2.0, 2.0, 0.5, 0.5, 20, 20), P(128, 128, 32, 0.01, 0.01, 0.1, 0), 1,
-         _lib.PIPE_EUNSUPPORTED),                                         # window wider than 64
-        (G(1.0, 1.0, 0.3 / 128, 0.5 / 128, 20, 20), good, 1, _lib.PIPE_EUNSUPPORTED),  # 2x0/h
+        # complex-FP16 spectra: transform form only, powers of two
+        (good_geo, P(96, 96, 256, 1 / 96, 1 / 96, 0.1, 2), 1, _lib.PIPE_EUNSUPPORTED),
+        # a window wider than 64 with more modes than the mode form holds
+        (G(2.0, 2.0, 0.5, 0.5, 40, 40), P(128, 128, 32, 0.01, 0.01, 0.1, 0), 1,
+         _lib.PIPE_EUNSUPPORTED),
+        # 2x0/h not an integer (a window for the transform form), 33 modes
+        (G(1.0, 1.0, 0.3 / 128, 0.5 / 128, 33, 20), good, 1, _lib.PIPE_EUNSUPPORTED),
     ]
     for geo, grid, igf, want in cases:
         st, h = _setup(L, geo, grid, igf)
@@ -89,6 +94,10 @@ def test_null_handle_and_pointers(L):
     assert L.pipe_poisson_adjoint(None, None, None, None) == _lib.PIPE_EINVAL
     assert L.pipe_poisson_solve_host(None, None, None, None) == _lib.PIPE_EINVAL
     assert L.pipe_green_spectrum(None, None, 0) == _lib.PIPE_EINVAL
+    assert L.pipe_mode_spectrum(None, None, 0) == _lib.PIPE_EINVAL
+    assert L.pipe_stage_modes(None, 0, None, None, None) == _lib.PIPE_EINVAL
+    v = [ctypes.c_int() for _ in range(5)]
+    assert L.pipe_mode_layout(None, *[ctypes.byref(x) for x in v]) == _lib.PIPE_EINVAL
     L.pipe_green_destroy(None)
 
 
