@@ -3,10 +3,13 @@
 
 Workload: one 128x128x1024 IGF solve (padded 256x256x2048), a = b = 1,
 sigma_perp = 0.15, sigma_z = 3 (sigma_z/sigma_x = 20), Lz = 8 sigma_z, M = 20,
-FP32 path; a step is one full solve (z transform, transverse stage with the
-four-term Green product, inverse z transform) of a synthetic Gaussian bunch
-resident in HBM.  L2 (129 MB) is flushed by a 256 MB write between steps and
-the flush is outside the timed events.
+FP32 path; a step is one full solve of a synthetic Gaussian bunch resident in
+HBM, in the handle's default form (the mode-space form at this size: the
+transverse transforms pruned to the 20 x 20 modes, the zero-padded z
+convolution per mode, the back-projection); the padded-transform form (z
+transform, transverse stage with the four-term Green product, inverse z
+transform) is timed beside it.  L2 (129 MB) is flushed by a 256 MB write
+between steps and the flush is outside the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,11 +41,17 @@ KERNEL_SOURCES = {
     "transverse": ["tdst_impl.cuh", "transverse_sym.cu", "fft_common.cuh", "solver.cuh"],
     "z_forward": ["zfft_impl.cuh", "zfft.cu", "fft_common.cuh", "solver.cuh"],
     "z_inverse": ["zfft_impl.cuh", "zfft.cu", "fft_common.cuh", "solver.cuh"],
+    "mode_project": ["modes_impl.cuh", "modes.cu", "modes.cuh"],
+    "mode_z": ["modes_impl.cuh", "modes.cu", "modes.cuh", "zfft_impl.cuh", "fft_common.cuh", "solver.cuh"],
+    "mode_back": ["modes_impl.cuh", "modes.cu", "modes.cuh"],
 }
 PROFILE_FILES = {
     "transverse": "transverse_dsts_pipe128x128x1024_igf_f32.md",
     "z_forward": "zfft_pipe128x128x1024_igf_f32.md",
     "z_inverse": "zfft_pipe128x128x1024_igf_f32.md",
+    "mode_project": "modes_pipe128x128x1024_igf_f32.md",
+    "mode_z": "modes_pipe128x128x1024_igf_f32.md",
+    "mode_back": "modes_pipe128x128x1024_igf_f32.md",
 }
 
 
@@ -53,6 +62,38 @@ def source_hash(kernel):
         with open(os.path.join(ROOT, "paper_1111_4971_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def bench_config(nx, ny, nz, world):
+    """The workload description both arms print."""
+    return {"workload": WORKLOAD, "grid": [nx, ny, nz], "padded": [2 * nx, 2 * ny, 2 * nz],
+            "green": "igf", "modes": 20, "sigma": [0.15, 0.15, 3.0], "parallelism": f"replicas{world}",
+            "l2": "flushed between steps (256 MB write, outside the timed events)"}
+
+
+def transform_alg_bytes(nx, ny, nz, esz=4):
+    """Algorithmic bytes per launch of the padded-transform form's kernels:
+    z forward reads rho and writes the (nz+1) x nx x ny half spectrum, the
+    transverse stage reads and writes every kz plane and reads the Green octant
+    plane, z inverse reads the spectrum and writes phi."""
+    plane = nx * ny * 2 * esz
+    green_plane = (nx + 1) * (ny + 1) * esz
+    return {"z_forward": nx * ny * nz * esz + (nz + 1) * plane,
+            "transverse": (nz + 1) * (2 * plane + green_plane),
+            "z_inverse": (nz + 1) * plane + nx * ny * nz * esz}
+
+
+def mode_alg_bytes(nx, ny, nz, mc, groups, esz=4):
+    """Algorithmic bytes per launch of the mode-space form's kernels: the
+    projection reads rho and writes one partial projection per group of x
+    rows, the z kernel reads the partials and the kernel spectra and writes
+    the convolved mode columns, the back-projection reads those (once per z
+    chunk) and writes phi."""
+    field = nx * ny * nz * esz
+    part = groups * mc * nz * esz
+    psi = mc * nz * esz
+    return {"mode_project": field + part, "mode_z": part + mc * (nz + 1) * esz + psi,
+            "mode_back": psi + field}
 
 
 def recorded_traffic(kernel):
@@ -224,12 +265,13 @@ def run_reference(args):
     timed, cores, _ = cpu_oracle_baseline(w, steps=args.steps, budget_s=REF_BUDGET_S, warmup=warm)
     total = sum(timed)
     value = len(timed) / total
+    nx, ny, nz = w["grid"].shape
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
+        "steps": len(timed), "steps_requested": args.steps, "warmup": warm,
+        "ms_per_step": 1e3 * total / len(timed),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [128, 128, 1024],
-                                        "padded": [256, 256, 2048], "green": "igf", "modes": 20},
+        "data": "synthetic", "config": bench_config(nx, ny, nz, world),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": f"{len(timed)} of the {args.steps} requested steps timed "
                                    f"({REF_BUDGET_S:.0f} s budget, {warm} warm-up solve), each one "
@@ -239,6 +281,22 @@ def run_reference(args):
     }
     print(json.dumps(line))
     return 0
+
+
+def time_stages(stages, names, steps, flush, stream):
+    """Each stage of `steps` solves timed with CUDA events on `stream`, L2
+    flushed before each solve (outside the events)."""
+    import torch
+    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        e = kev[i]
+        e[0].record(stream)
+        for k, fn in enumerate(stages):
+            fn()
+            e[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return {n: [e[k].elapsed_time(e[k + 1]) for e in kev] for k, n in enumerate(names)}
 
 
 def bench_batched(args, count=96):
@@ -354,15 +412,30 @@ def run_ours(args):
         s32.autotune()
     rho = torch.tensor(rho_np, dtype=torch.float32, device=dev)
     phi = s32.empty()
-    spec = s32.spectrum_buffer()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()
+    modes_form = s32.plan["t_kind"] == 3
+    if modes_form:
+        mx, mxp, myp, fold, groups = s32.mode_layout()
+        part, psi = s32.mode_buffers()
+        stage_names = ["mode_project", "mode_z", "mode_back"]
+        stages = [lambda: s32.stage_modes(0, rho, part), lambda: s32.stage_modes(1, part, psi),
+                  lambda: s32.stage_modes(2, psi, phi)]
+        alg_bytes = mode_alg_bytes(nx, ny, nz, mxp * myp, groups)
+    else:
+        spec = s32.spectrum_buffer()
+        stage_names = ["z_forward", "transverse", "z_inverse"]
+        stages = [lambda: s32.stage_z_forward(rho, spec), lambda: s32.stage_transverse(spec),
+                  lambda: s32.stage_z_inverse(spec, phi)]
+        alg_bytes = transform_alg_bytes(nx, ny, nz)
 
     for _ in range(args.warmup):
         s32.solve(rho, phi)
     barrier(world)
     if args.solves_only:                       # profiling target: K plain solves
         for _ in range(args.steps):
+            if args.flush:
+                flush.fill_(0.0)
             s32.solve(rho, phi)
         barrier(world)
         if rank == 0:
@@ -386,24 +459,9 @@ def run_ours(args):
     t_wall = time.perf_counter() - t_wall
     solve_ms = [a.elapsed_time(b) for a, b in ev]
     # ---- the same K steps through the stage entry points, per kernel -------
-    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        e = kev[i]
-        e[0].record(stream)
-        s32.stage_z_forward(rho, spec)
-        e[1].record(stream)
-        s32.stage_transverse(spec)
-        e[2].record(stream)
-        s32.stage_z_inverse(spec, phi)
-        e[3].record(stream)
+    k_ms = time_stages(stages, stage_names, args.steps, flush, stream)
     barrier(world)
     clocks = sampler.stop()
-    k_ms = {
-        "z_forward": [e[0].elapsed_time(e[1]) for e in kev],
-        "transverse": [e[1].elapsed_time(e[2]) for e in kev],
-        "z_inverse": [e[2].elapsed_time(e[3]) for e in kev],
-    }
     total_ms = max_over_ranks(world, sum(solve_ms))
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(world, args.steps, total_ms)
@@ -438,27 +496,20 @@ def run_ours(args):
     serial_value = whole_job_rate(world, args.steps, max_over_ranks(world, sum(serial_ms)))
     nbytes = nx * ny * nz * 4
 
-    # ---- roofline of the dominant kernel ---------------------------------
+    # ---- roofline of the dominant kernel and of the whole solve ----------
     peak, peak_kind = peaks()
     means = {k: statistics.mean(v) for k, v in k_ms.items()}
     dom = max(means, key=means.get)
-    plane = nx * ny * 8
-    green_plane = (nx + 1) * (ny + 1) * 4
-    alg_bytes = {
-        "z_forward": nx * ny * nz * 4 + (nz + 1) * plane,
-        "transverse": (nz + 1) * (2 * plane + green_plane),
-        "z_inverse": (nz + 1) * plane + nx * ny * nz * 4,
-    }
     achieved = {k: alg_bytes[k] / (means[k] * 1e-3) / 1e9 for k in means}
+    solve_bytes = sum(alg_bytes.values())
     b_pad = 4 * (2 * nx) * (2 * ny) * (nz + 1) * 8
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [nx, ny, nz], "padded": [2 * nx, 2 * ny, 2 * nz],
-                   "green": "igf", "modes": 20, "sigma": [0.15, 0.15, 3.0],
-                   "parallelism": f"replicas{world}",
-                   "l2": "flushed between steps (256 MB write, outside the timed events)"},
+        "config": bench_config(nx, ny, nz, world),
+        "form": "modes" if modes_form else "transforms",
+        "plan": s32.plan,
         "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved[dom], "peak": peak,
                      "unit": "GB/s", "frac": achieved[dom] / peak, "traffic": recorded_traffic(dom),
@@ -467,6 +518,12 @@ def run_ours(args):
         "kernels_ms": means,
         "kernels_gbs": achieved,
         "kernels_source_sha256": {k: source_hash(k) for k in KERNEL_SOURCES},
+        # the whole solve against its own algorithmic bytes (the sum over its kernels)
+        "solve_alg_bytes": solve_bytes,
+        "solve_gbs": solve_bytes / (ms_per_step * 1e-3) / 1e9,
+        "solve_frac": solve_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
+        # the metric's nominal bytes: the padded transforms' half spectra read and
+        # written twice (4 |S|); neither form moves them, so this is not a traffic
         "b_pad": {"bytes": b_pad, "gbs": b_pad / (ms_per_step * 1e-3) / 1e9,
                   "frac_of_measured": b_pad / (ms_per_step * 1e-3) / 1e9 / peak,
                   "frac_of_8tbs": b_pad / (ms_per_step * 1e-3) / 1e9 / 8000.0},
@@ -481,6 +538,39 @@ def run_ours(args):
         # wait of the staged transverse kernel gave up)
         "device_status": s32.status(),
     }
+
+    # ---- the padded-transform form of the same solve, same steps ---------
+    if modes_form and not args.quick:
+        st32 = PipeSolver(geom, grid, igf=True, dtype=torch.float32)
+        st32.set_plan(z_warps=4, z_pipe=0, t_h=1, t_threads=256, t_kind=2)
+        spec = st32.spectrum_buffer()
+        for _ in range(args.warmup):
+            st32.solve(rho, phi)
+        tms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st32.solve(rho, phi)
+            b.record(stream)
+            tms.append((a, b))
+        torch.cuda.synchronize()
+        t_ms = statistics.mean(a.elapsed_time(b) for a, b in tms)
+        tk = time_stages([lambda: st32.stage_z_forward(rho, spec), lambda: st32.stage_transverse(spec),
+                          lambda: st32.stage_z_inverse(spec, phi)], ["z_forward", "transverse", "z_inverse"],
+                         args.steps, flush, stream)
+        tmeans = {k: statistics.mean(v) for k, v in tk.items()}
+        tbytes = transform_alg_bytes(nx, ny, nz)
+        tdom = max(tmeans, key=tmeans.get)
+        tach = {k: tbytes[k] / (tmeans[k] * 1e-3) / 1e9 for k in tmeans}
+        line["transform_form"] = {
+            "plan": st32.plan, "solves_per_s": 1e3 / t_ms, "ms": t_ms, "kernels_ms": tmeans,
+            "kernels_gbs": tach, "solve_alg_bytes": sum(tbytes.values()),
+            "solve_frac": sum(tbytes.values()) / (t_ms * 1e-3) / 1e9 / peak,
+            "roofline": {"bound": "hbm", "kernel": tdom, "achieved": tach[tdom], "peak": peak, "unit": "GB/s",
+                         "frac": tach[tdom] / peak, "traffic": recorded_traffic(tdom),
+                         "alg_bytes_per_launch": tbytes[tdom], "kernel_ms": tmeans[tdom]}}
+        st32.close()
 
     # ---- FP64 path, free-space (Hockney) comparison, accuracy -------------
     if rank == 0 and not args.quick:
@@ -533,7 +623,24 @@ def run_ours(args):
         p16 = phi16.double().cpu().numpy()
         line["fp16_spectra"] = {"solves_per_s": 1e3 / statistics.median(t16), "ms": statistics.median(t16),
                                 "rel_l2_vs_fp64": float(np.linalg.norm(p16 - p64) / np.linalg.norm(p64))}
-        line["fp64"] = {"solves_per_s": 1e3 / statistics.median(t64), "ms": statistics.median(t64)}
+        line["fp64"] = {"solves_per_s": 1e3 / statistics.median(t64), "ms": statistics.median(t64),
+                        "plan": s64.plan}
+        # the FP64 padded-transform form (n-point transverse routine, global scratch planes)
+        s64t = PipeSolver(geom, grid, igf=True, dtype=torch.float64)
+        s64t.set_plan(z_warps=8, z_pipe=0, t_h=1, t_threads=256, t_kind=1)
+        s64t.solve(rho64, phi64)
+        t64t = []
+        for i in range(3):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s64t.solve(rho64, phi64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t64t.append(a.elapsed_time(b))
+        line["fp64_transform_form"] = {"solves_per_s": 1e3 / statistics.median(t64t),
+                                       "ms": statistics.median(t64t), "plan": s64t.plan}
+        s64t.close()
         line["fp32_rel_l2_vs_fp64"] = err
         line["hockney_fp32"] = {"solves_per_s": 1e3 / statistics.median(th), "ms": statistics.median(th)}
         if args.check_oracle:
@@ -575,12 +682,41 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--solves-only", action="store_true",
                     help="setup, warm-up and K plain solves only (profiling target)")
+    ap.add_argument("--flush", action="store_true",
+                    help="with --solves-only: flush L2 before every solve, as the timed steps do")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    how, what = replica_launch(args.gpus, os.environ)
+    if how == "error":
+        print(what, file=sys.stderr)
+        return 2
+    if how == "spawn":
+        return subprocess.call(what)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
+
+
+def replica_launch(gpus, env):
+    """How to run N replicas: ("run", None) in this process when the launcher's
+    WORLD_SIZE matches --gpus (or N = 1 with no launcher); ("spawn", command)
+    to start N processes, one per GPU, through torch.distributed.run when N > 1
+    and no launcher did; ("error", message) when WORLD_SIZE and --gpus differ."""
+    world = env.get("WORLD_SIZE")
+    if world is None:
+        if gpus <= 1:
+            return "run", None
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)]
+        return "spawn", cmd + sys.argv[1:]
+    if int(world) != gpus:
+        return "error", f"bench.py: --gpus {gpus} but WORLD_SIZE={world} processes were launched"
+    return "run", None
 
 
 if __name__ == "__main__":

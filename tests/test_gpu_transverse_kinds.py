@@ -129,6 +129,7 @@ def test_npoint_plan_refused_where_it_does_not_apply():
         s.set_plan(z_warps=8, z_pipe=0, t_h=1, t_threads=256, t_kind=1)
     geom, grid = CELL["sq128x128x32"]
     s = solver(geom, grid, 1, torch.float64)
+    s.set_plan(z_warps=8, z_pipe=0, t_h=1, t_threads=256, t_kind=1)
     assert s.plan["t_kind"] == 1                         # FP64 128^2: global scratch planes
     with pytest.raises(PipeError):                      # one CTA per plane only
         s.set_plan(z_warps=8, z_pipe=0, t_h=2, t_threads=256, t_kind=1)

@@ -69,3 +69,21 @@ def test_single_process_rate_and_reference_arm_only_on_rank_zero(monkeypatch):
     monkeypatch.setattr(bench, "cpu_oracle_baseline", lambda *a, **k: called.append(1))
     assert bench.run_reference(Args()) == 0
     assert not called
+
+
+def test_replica_launch_spawns_or_refuses_on_a_mismatch():
+    """`bench.py --gpus N` without a launcher starts N processes itself
+    (torch.distributed.run, 127.0.0.1), runs in place under a launcher whose
+    WORLD_SIZE is N, and exits with an error when the two differ."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.replica_launch(1, {}) == ("run", None)
+    how, cmd = bench.replica_launch(4, {})
+    assert how == "spawn"
+    assert cmd[1:3] == ["-m", "torch.distributed.run"]
+    assert "--nproc-per-node=4" in cmd and "127.0.0.1" in cmd
+    assert cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
+    assert bench.replica_launch(2, {"WORLD_SIZE": "2"}) == ("run", None)
+    how, msg = bench.replica_launch(8, {"WORLD_SIZE": "1"})
+    assert how == "error" and "WORLD_SIZE=1" in msg
