@@ -6,17 +6,31 @@
 // every warp load or store of the fields is a run of 32 z values.
 //   projection:      A[x][n][z] = sum_{j < ny/2} Sy[j][n] (rho[x][j][z] +- rho[x][ny-1-j][z])
 //                    (+ for odd n, - for even n), one thread per (x row, z) with
-//                    the y-mode table as a kernel parameter (constant bank);
-//                    then the CTA's rows summed against the x modes and the
-//                    cluster's CTAs added up through distributed shared memory,
-//                    in rank order (as mode_project).
-//   back-projection: B[x][n][z] = sum_m Sx[x][m] psi[m][n][z] (psi chunk in shared
-//                    memory, computed once per CTA); each thread holds a 2 x MYP
-//                    tile (two x rows, all y modes) so that each y-mode value read
-//                    from shared memory (16-byte broadcasts) serves two FMAs, and
-//                    the two warps of an x pair split the rows: phi[x][j][z] = O + E and
-//                    phi[x][ny-1-j][z] = O - E with O, E the sums of
-//                    Sy[j][n] B[x][n][z] over odd and even n.
+//                    the y-mode table as a kernel parameter (constant bank) and
+//                    the warp's field rows staged through a cp.async ring; then
+//                    the x-mode sums over the CTA's rows,
+//                    P[m][n][z] = sum_x Sx[x][m] A[x][n][z], and the cluster's
+//                    CTAs added up through distributed shared memory, in rank
+//                    order (as mode_project).
+//   back-projection: B[x][n][z] = sum_m Sx[x][m] psi[m][n][z] (psi chunk in
+//                    shared memory, computed once per CTA), then
+//                    phi[x][j][z] = O + E and phi[x][ny-1-j][z] = O - E with O, E
+//                    the sums of Sy[j][n] B[x][n][z] over odd and even n, the
+//                    table again a kernel parameter; a thread holds the B values
+//                    of two x rows (up to 20 y-mode slots; the two warps of an x
+//                    pair split the rows j) or of one.
+//
+// The two x-mode sums are small matrix products per CTA, [(n, z)] x [x] by
+// [x] x [m] and [(n, z)] x [m] by [m] x [x], and run on the tensor cores as
+// warp-level TF32 MMA (mma.sync m16n8k8) at FP32 accuracy: each operand v is
+// split as v = hi + lo, hi = tf32(v) (round to nearest, 11 significant bits),
+// lo = tf32(v - hi), and a product is taken as lo*hi + hi*lo + hi*hi with FP32
+// accumulation (the dropped lo*lo is below 2^-22 of it).  Fragment layout of
+// m16n8k8 (lane = 4g + t): A (16 x 8, row major) (g, t), (g+8, t), (g, t+4),
+// (g+8, t+4); B (8 x 8, column major) (t, g), (t+4, g); C (16 x 8) (g, 2t),
+// (g, 2t+1), (g+8, 2t), (g+8, 2t+1).  A tile's 16 rows are 16 z of one n; the
+// shared-memory rows are padded so that the fragment reads and writes of a
+// warp fall on 32 distinct banks.
 #include "modes.cuh"
 #include "modes_impl.cuh"
 
@@ -28,73 +42,160 @@ constexpr int kW = 16;                    // warps per CTA
 constexpr int kX = 16;                    // x rows per CTA
 constexpr int kZC = 32;                   // z values per CTA
 
-__device__ __forceinline__ void row4(const float* p, float (&s)[4]) {
-  const float4 v = *reinterpret_cast<const float4*>(p);
-  s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+// d += a * b on one m16n8k8 tile
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// d += (ah + al) * (bh + bl), the three terms that matter, small ones first
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                     const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
+  mma_tf32(d, al[0], al[1], al[2], al[3], bh[0], bh[1]);
+  mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
+  mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
+}
+// the A fragment of rows (g, g+8) and columns (k, k+4) of a row-major tile
+// whose column k + 1 is cs floats after column k (p already at row g, column t);
+// columns switched off read as zero
+__device__ __forceinline__ void load_a(const float* p, int cs, bool on_lo, bool on_hi, uint32_t (&ah)[4],
+                                       uint32_t (&al)[4]) {
+  split_tf32(on_lo ? p[0] : 0.f, ah[0], al[0]);
+  split_tf32(on_lo ? p[8] : 0.f, ah[1], al[1]);
+  split_tf32(on_hi ? p[4 * cs] : 0.f, ah[2], al[2]);
+  split_tf32(on_hi ? p[4 * cs + 8] : 0.f, ah[3], al[3]);
 }
 
 }  // namespace
 
-// two CTAs per SM (64 registers) up to 20 y-mode slots, one beyond
-template <int MYP>
-constexpr int fast_min_blocks() { return MYP <= 20 ? 2 : 1; }
-
-// the y-mode table as a kernel parameter: with the y loop unrolled, each
+// the y-mode table as a kernel parameter: with the y loops unrolled, each
 // value is read at a compile-time offset of the constant bank
 template <int NYH, int MYP>
 struct SyTab {
   float s[NYH * MYP];
 };
 
+// Per-warp staging of the projection's field rows: a ring of kStages buffers
+// of kPairs rows j and their mirrors ny-1-j (32 z each), filled by cp.async so
+// that the next rows of each warp are in flight without holding registers.  A
+// warp's ring and, after its y sums, its row of A[x][n][z] share one slot of
+// shared memory (slot_a floats, 8 beyond a multiple of 32 so that the x-mode
+// pass's fragment rows t and t + 4 fall on different banks).
+constexpr int kPairs = 4;
+constexpr int kStages = 3;
+constexpr int kRing = kStages * 2 * kPairs * kZC;
+template <int MYP>
+constexpr int slot_a() { return ((kRing > MYP * kZC ? kRing : MYP * kZC) + 31) / 32 * 32 + 8; }
+// row stride (floats) of the back-projection's psi chunk [m][n][z] (8 beyond a
+// multiple of 32) and of its B[x][n][z] (4 beyond: rows 2t and 2t + 1 apart)
+template <int MYP> constexpr int rows_p() { return MYP * kZC + 8; }
+template <int MYP> constexpr int rows_b() { return MYP * kZC + 4; }
+// column stride of the projection's x-mode sums P[m][n][z] (the DSMEM
+// reduction reads runs of consecutive z)
+constexpr int kCS = kZC + 1;
+// x rows per thread of the back-projection's y sums (its registers hold
+// XR * MYP values of B)
+template <int MYP>
+constexpr int back_rows_per_thread() { return MYP <= 20 ? 2 : 1; }
+
 // one thread per (x row, z): the 16 warps of a CTA take its 16 x rows
 template <int NYH, int MYP>
 __global__ void __launch_bounds__(32 * kW, 2)
     mode_project_fast_kernel(ModeArgs<float> a, const __grid_constant__ SyTab<NYH, MYP> tab) {
+  constexpr int RS = slot_a<MYP>();
+  constexpr int KS = kX / 8;                                   // k steps over the CTA's x rows
+  constexpr int NS = NYH / kPairs;                             // ring stages over the half rows
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* abuf = reinterpret_cast<float*>(smem_raw);            // [16][MYP][32]
-  float* red = abuf + kX * MYP * kZC;                          // [mc][32]
-  float* sxs = red + size_t(a.mc) * kZC;                       // [16][mxp]
+  float* abuf = reinterpret_cast<float*>(smem_raw);            // [16][RS]: ring, then A[x][n][z]
+  float* red = abuf + kX * RS;                                 // [mc][33]: P[m][n][z]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
   const int z0 = int(blockIdx.x) * kZC;
   const int xb0 = int(blockIdx.y) * kX;
   const int ny = 2 * NYH;
-  for (int i = threadIdx.x; i < kX * a.mxp; i += 32 * kW) sxs[i] = a.sx[size_t(xb0) * a.mxp + i];
 
-  const float* col = a.rho + size_t(xb0 + warp) * ny * a.nz + z0 + lane;
+  float* ring = abuf + warp * RS;
+  const float* xrow = a.rho + size_t(xb0 + warp) * ny * a.nz + z0;
+  // stage s: rows s*kPairs + r (r < kPairs) and their mirrors, 16 bytes a lane a copy
+  auto issue = [&](int s) {
+    float* buf = ring + (s % kStages) * (2 * kPairs * kZC);
+#pragma unroll
+    for (int k = 0; k < 2 * kPairs * kZC / 4 / 32; ++k) {
+      const int idx = k * 32 + lane, r = idx >> 3, piece = idx & 7;
+      const int j = r < kPairs ? s * kPairs + r : ny - 1 - (s * kPairs + r - kPairs);
+      cp_async16(buf + r * kZC + 4 * piece, xrow + size_t(j) * a.nz + 4 * piece);
+    }
+    cp_async_commit();
+  };
   float acc[MYP];
 #pragma unroll
   for (int n = 0; n < MYP; ++n) acc[n] = 0.f;
 #pragma unroll
-  for (int j = 0; j < NYH; ++j) {
-    const float u = __ldg(&col[size_t(j) * a.nz]);
-    const float v = __ldg(&col[size_t(ny - 1 - j) * a.nz]);
-    const float p = u + v, q = u - v;
+  for (int s = 0; s < kStages - 1; ++s) issue(s);
 #pragma unroll
-    for (int n = 0; n < MYP; ++n) acc[n] = fmaf(tab.s[j * MYP + n], n < MYP / 2 ? p : q, acc[n]);
+  for (int s = 0; s < NS; ++s) {
+    // groups committed: stages 0 .. min(s + kStages - 2, NS - 1); stage s must be in
+    if (s + kStages - 1 <= NS) cp_async_wait<kStages - 2>();
+    else cp_async_wait<0>();
+    __syncwarp();
+    if (s + kStages - 1 < NS) issue(s + kStages - 1);          // the buffer read at stage s - 1
+    const float* buf = ring + (s % kStages) * (2 * kPairs * kZC);
+#pragma unroll
+    for (int r = 0; r < kPairs; ++r) {
+      const float u = buf[r * kZC + lane], v = buf[(kPairs + r) * kZC + lane];
+      const float p = u + v, q = u - v;
+      const int j = s * kPairs + r;
+#pragma unroll
+      for (int n = 0; n < MYP; ++n) acc[n] = fmaf(tab.s[j * MYP + n], n < MYP / 2 ? p : q, acc[n]);
+    }
   }
+  __syncwarp();                                                // ring reads done before A overwrites it
 #pragma unroll
-  for (int n = 0; n < MYP; ++n) abuf[(warp * MYP + n) * kZC + lane] = acc[n];
+  for (int n = 0; n < MYP; ++n) abuf[warp * RS + n * kZC + lane] = acc[n];
+  const int mtiles = (a.mxp + 7) / 8;
+  const float* sxb = a.sx + size_t(xb0 + t) * a.mxp + g;     // B[k = x][col = m] = Sx[xb0 + x][m]
   __syncthreads();
 
-  // x modes over the CTA's rows: warp w takes (n, m quad) units w, w + 16, ...
-  const int quads = a.mxp / 4;
+  // P^T[(n, z)][m] = sum_x A[x][n][z] Sx[x][m]: tile = (n, 16 z), warp-strided
 #pragma unroll 1
-  for (int u = warp; u < MYP * quads; u += kW) {
-    const int n = u % MYP, q4 = u / MYP;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll 4
-    for (int xl = 0; xl < kX; ++xl) {
-      const float av = abuf[(xl * MYP + n) * kZC + lane];
-      const float4 sx4 = *reinterpret_cast<const float4*>(&sxs[xl * a.mxp + 4 * q4]);
-      s0 = fmaf(sx4.x, av, s0);
-      s1 = fmaf(sx4.y, av, s1);
-      s2 = fmaf(sx4.z, av, s2);
-      s3 = fmaf(sx4.w, av, s3);
+  for (int tile = warp; tile < 2 * MYP; tile += kW) {
+    const int n = tile >> 1, zz = (tile & 1) * 16;
+    uint32_t ah[KS][4], al[KS][4];
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) load_a(abuf + (8 * ks + t) * RS + n * kZC + zz + g, RS, true, true, ah[ks], al[ks]);
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      if (nt < mtiles) {
+        const bool on = 8 * nt + g < a.mxp;
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+          uint32_t bh[2], bl[2];
+          split_tf32(on ? __ldg(sxb + (8 * ks) * a.mxp + 8 * nt) : 0.f, bh[0], bl[0]);
+          split_tf32(on ? __ldg(sxb + (8 * ks + 4) * a.mxp + 8 * nt) : 0.f, bh[1], bl[1]);
+          mma3(d, ah[ks], al[ks], bh, bl);
+        }
+        const int m = 8 * nt + 2 * t;                  // mxp is a multiple of 4: m, m + 1 both in or out
+        if (m < a.mxp) {
+          float* r = red + (m * MYP + n) * kCS + zz + g;
+          r[0] = d[0];
+          r[MYP * kCS] = d[1];
+          r[8] = d[2];
+          r[MYP * kCS + 8] = d[3];
+        }
+      }
     }
-    red[((4 * q4 + 0) * MYP + n) * kZC + lane] = s0;
-    red[((4 * q4 + 1) * MYP + n) * kZC + lane] = s1;
-    red[((4 * q4 + 2) * MYP + n) * kZC + lane] = s2;
-    red[((4 * q4 + 3) * MYP + n) * kZC + lane] = s3;
   }
 
   // the cluster's CTAs added up in rank order, each CTA a slice of the columns
@@ -106,99 +207,128 @@ __global__ void __launch_bounds__(32 * kW, 2)
   float* out = a.part + size_t(blockIdx.y / ncl) * a.mc * a.nz + z0 + lane;
 #pragma unroll 1
   for (int c = c0 + warp; c < c1; c += kW) {
+    float v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = r < ncl ? cl.map_shared_rank(red, r)[c * kCS + lane] : 0.f;
     float sum = 0.f;
-#pragma unroll 1
-    for (int r = 0; r < ncl; ++r) sum += cl.map_shared_rank(red, r)[c * kZC + lane];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sum += v[r];
     out[size_t(c) * a.nz] = sum;
   }
   cl.sync();
 }
 
-template <int NYH, int MYP>
-__global__ void __launch_bounds__(32 * kW, fast_min_blocks<MYP>()) mode_back_fast_kernel(ModeArgs<float> a) {
-  constexpr int Q = NYH / 2;
+// rows j = J0 .. J0 + NJ - 1 of XR x rows (xs apart) and their mirrors
+// ny-1-j, the y-mode table read at compile-time offsets of the constant bank
+template <int NYH, int MYP, int XR, int J0, int NJ>
+__device__ __forceinline__ void back_rows(const float (&bv)[XR][MYP], const SyTab<NYH, MYP>& tab, float* base,
+                                          int nz, int xs) {
   constexpr int H = MYP / 2;
+  float* lo = base + J0 * nz;
+  float* hi = base + (2 * NYH - 1 - J0) * nz;
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj) {
+    const int j = J0 + jj;
+    float o[XR], e[XR];
+#pragma unroll
+    for (int i = 0; i < XR; ++i) o[i] = e[i] = 0.f;
+#pragma unroll
+    for (int n = 0; n < MYP; ++n) {
+      const float s = tab.s[j * MYP + n];
+#pragma unroll
+      for (int i = 0; i < XR; ++i) {
+        if (n < H) o[i] = fmaf(s, bv[i][n], o[i]);
+        else e[i] = fmaf(s, bv[i][n], e[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < XR; ++i) {
+      lo[i * xs] = o[i] + e[i];
+      hi[i * xs] = o[i] - e[i];
+    }
+    lo += nz;
+    hi -= nz;
+    // one running pointer per mirror, not one precomputed address per row
+    asm volatile("" : "+l"(lo), "+l"(hi));
+  }
+}
+
+template <int NYH, int MYP>
+__global__ void __launch_bounds__(32 * kW, 2)
+    mode_back_fast_kernel(ModeArgs<float> a, const __grid_constant__ SyTab<NYH, MYP> tab) {
+  constexpr int RS = rows_p<MYP>(), BS = rows_b<MYP>();
+  constexpr int XT = kX / 8;                         // n tiles over the CTA's x rows
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* ps = reinterpret_cast<float*>(smem_raw);    // psi chunk [mx * MYP][32]
-  float* bvs = ps + size_t(a.mx) * MYP * kZC;        // x-mode sums [16][MYP][32]
-  float* sxs = bvs + kX * MYP * kZC;                 // [16][mxp]
-  float* sy = sxs + kX * a.mxp;                      // [NYH][MYP]
+  float* ps = reinterpret_cast<float*>(smem_raw);    // psi chunk [mx][RS]: psi[m][n][z]
+  float* bvs = ps + size_t(a.mx) * RS;               // x-mode sums [16][BS]: B[x][n][z]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
   const int pair = warp % (kW / 2), half = warp / (kW / 2);
   const int z0 = int(blockIdx.x) * kZC;
   const int xb0 = int(blockIdx.y) * kX;
   const int ny = 2 * NYH;
   for (int idx = threadIdx.x; idx < a.mx * MYP * (kZC / 4); idx += 32 * kW) {
     const int c = idx / (kZC / 4), piece = idx % (kZC / 4);
-    cp_async16(ps + size_t(c) * kZC + 4 * piece, a.psi + size_t(c) * a.nz + z0 + 4 * piece);
+    cp_async16(ps + (c / MYP) * RS + (c % MYP) * kZC + 4 * piece, a.psi + size_t(c) * a.nz + z0 + 4 * piece);
   }
   cp_async_commit();
-  for (int i = threadIdx.x; i < kX * a.mxp; i += 32 * kW) sxs[i] = a.sx[size_t(xb0) * a.mxp + i];
-  for (int i = threadIdx.x; i < NYH * MYP; i += 32 * kW) sy[i] = a.sy[i];
+  const int ksteps = (a.mxp + 7) / 8;
+  const float* sxb = a.sx + size_t(xb0 + g) * a.mxp + t;     // B[k = m][col = x] = Sx[xb0 + x][m]
   cp_async_wait<0>();
   __syncthreads();
 
-  // x-mode sums of the pair's two rows, this warp's half of the y modes
-  {
-    float b[2][H];
+  // B^T[(n, z)][x] = sum_m psi[m][n][z] Sx[x][m]: tile = (n, 16 z), warp-strided
+#pragma unroll 1
+  for (int tile = warp; tile < 2 * MYP; tile += kW) {
+    const int n = tile >> 1, zz = (tile & 1) * 16;
+    float d[XT][4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int nt = 0; nt < XT; ++nt) d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.f;
 #pragma unroll
-      for (int n = 0; n < H; ++n) b[i][n] = 0.f;
-#pragma unroll 2
-    for (int m = 0; m < a.mx; ++m) {
-      const float s0 = sxs[(2 * pair) * a.mxp + m], s1 = sxs[(2 * pair + 1) * a.mxp + m];
+    for (int ks = 0; ks < 4; ++ks) {
+      if (ks < ksteps) {
+        // rows m >= mx of psi are zero (read as zero; the rows stay inside
+        // the buffer: m < mx + 8 and B's 16 rows follow the chunk)
+        const int m = 8 * ks + t;
+        uint32_t ah[4], al[4];
+        load_a(ps + m * RS + n * kZC + zz + g, RS, m < a.mx, m + 4 < a.mx, ah, al);
 #pragma unroll
-      for (int n = 0; n < H; ++n) {
-        const float pv = ps[(m * MYP + half * H + n) * kZC + lane];
-        b[0][n] = fmaf(s0, pv, b[0][n]);
-        b[1][n] = fmaf(s1, pv, b[1][n]);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int n = 0; n < H; ++n) bvs[((2 * pair + i) * MYP + half * H + n) * kZC + lane] = b[i][n];
-  }
-  __syncthreads();
-
-  float bv[2][MYP];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int n = 0; n < MYP; ++n) bv[i][n] = bvs[((2 * pair + i) * MYP + n) * kZC + lane];
-  // this warp's half of the rows j (and their mirrors); 32-bit offsets from
-  // the pair's first row (the field is below 2^31 values)
-  float* base = a.phi + size_t(xb0 + 2 * pair) * ny * a.nz + z0 + lane;
-  const int xs = ny * a.nz, step = a.nz;
-  int lo = half * Q * a.nz;
-  int hi = (ny - 1 - half * Q) * a.nz;
-#pragma unroll 4
-  for (int jj = 0; jj < Q; ++jj) {
-    const float* srow = sy + (half * Q + jj) * MYP;
-    float o0 = 0.f, e0 = 0.f, o1 = 0.f, e1 = 0.f;
-#pragma unroll
-    for (int g = 0; g < MYP; g += 4) {
-      float s[4];
-      row4(srow + g, s);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (g + k < H) {
-          o0 = fmaf(s[k], bv[0][g + k], o0);
-          o1 = fmaf(s[k], bv[1][g + k], o1);
-        } else {
-          e0 = fmaf(s[k], bv[0][g + k], e0);
-          e1 = fmaf(s[k], bv[1][g + k], e1);
+        for (int nt = 0; nt < XT; ++nt) {
+          uint32_t bh[2], bl[2];
+          const float* sp = sxb + size_t(8 * nt) * a.mxp + 8 * ks;
+          split_tf32(m < a.mxp ? __ldg(sp) : 0.f, bh[0], bl[0]);
+          split_tf32(m + 4 < a.mxp ? __ldg(sp + 4) : 0.f, bh[1], bl[1]);
+          mma3(d[nt], ah, al, bh, bl);
         }
       }
     }
-    base[lo] = o0 + e0;
-    base[hi] = o0 - e0;
-    base[lo + xs] = o1 + e1;
-    base[hi + xs] = o1 - e1;
-    lo += step;
-    hi -= step;
+#pragma unroll
+    for (int nt = 0; nt < XT; ++nt) {
+      float* r = bvs + (8 * nt + 2 * t) * BS + n * kZC + zz + g;
+      r[0] = d[nt][0];
+      r[BS] = d[nt][1];
+      r[8] = d[nt][2];
+      r[BS + 8] = d[nt][3];
+    }
   }
+  __syncthreads();
+
+  // XR x rows a thread: two (the two warps of an x pair split the rows j)
+  // up to 20 y-mode slots, else one (a warp takes all rows j of its x row)
+  constexpr int XR = back_rows_per_thread<MYP>();
+  float bv[XR][MYP];
+  const int x0 = XR == 2 ? 2 * pair : warp;
+#pragma unroll
+  for (int i = 0; i < XR; ++i)
+#pragma unroll
+    for (int n = 0; n < MYP; ++n) bv[i][n] = bvs[(x0 + i) * BS + n * kZC + lane];
+  float* base = a.phi + size_t(xb0 + x0) * ny * a.nz + z0 + lane;
+  if (XR == 1)
+    back_rows<NYH, MYP, XR, 0, NYH>(bv, tab, base, a.nz, ny * a.nz);
+  else if (half == 0)
+    back_rows<NYH, MYP, XR, 0, NYH / 2>(bv, tab, base, a.nz, ny * a.nz);
+  else
+    back_rows<NYH, MYP, XR, NYH / 2, NYH / 2>(bv, tab, base, a.nz, ny * a.nz);
 }
 
 namespace {
@@ -213,11 +343,11 @@ template <int NYH, int MYP>
 cudaError_t launch_fast(int which, const ModeArgs<float>& a, const float* sy_host, cudaStream_t st) {
   const int xblocks = a.nx / kX;
   const dim3 grid(unsigned(a.nz / kZC), unsigned(xblocks));
+  SyTab<NYH, MYP> tab;
+  for (int i = 0; i < NYH * MYP; ++i) tab.s[i] = sy_host[i];
   cudaError_t e;
   if (which == 0) {
-    SyTab<NYH, MYP> tab;
-    for (int i = 0; i < NYH * MYP; ++i) tab.s[i] = sy_host[i];
-    const size_t smem = sizeof(float) * (size_t(kX) * MYP * kZC + size_t(a.mc) * kZC + size_t(kX) * a.mxp);
+    const size_t smem = sizeof(float) * (size_t(kX) * slot_a<MYP>() + size_t(a.mc) * kCS);
     void (*kern)(ModeArgs<float>, const SyTab<NYH, MYP>) = mode_project_fast_kernel<NYH, MYP>;
     if ((e = big_smem(kern, smem)) != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -234,11 +364,10 @@ cudaError_t launch_fast(int which, const ModeArgs<float>& a, const float* sy_hos
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, a, tab);
   }
-  const size_t smem = sizeof(float) * (size_t(a.mx) * MYP * kZC + size_t(kX) * MYP * kZC + size_t(kX) * a.mxp +
-                                       size_t(NYH) * MYP);
-  void (*kern)(ModeArgs<float>) = mode_back_fast_kernel<NYH, MYP>;
+  const size_t smem = sizeof(float) * (size_t(a.mx) * rows_p<MYP>() + size_t(kX) * rows_b<MYP>());
+  void (*kern)(ModeArgs<float>, const SyTab<NYH, MYP>) = mode_back_fast_kernel<NYH, MYP>;
   if ((e = big_smem(kern, smem)) != cudaSuccess) return e;
-  kern<<<grid, 32 * kW, smem, st>>>(a);
+  kern<<<grid, 32 * kW, smem, st>>>(a, tab);
   return cudaGetLastError();
 }
 
