@@ -41,9 +41,9 @@ KERNEL_SOURCES = {
     "transverse": ["tdst_impl.cuh", "transverse_sym.cu", "fft_common.cuh", "solver.cuh"],
     "z_forward": ["zfft_impl.cuh", "zfft.cu", "fft_common.cuh", "solver.cuh"],
     "z_inverse": ["zfft_impl.cuh", "zfft.cu", "fft_common.cuh", "solver.cuh"],
-    "mode_project": ["modes_impl.cuh", "modes.cu", "modes.cuh"],
-    "mode_z": ["modes_impl.cuh", "modes.cu", "modes.cuh", "zfft_impl.cuh", "fft_common.cuh", "solver.cuh"],
-    "mode_back": ["modes_impl.cuh", "modes.cu", "modes.cuh"],
+    "mode_project": ["modes_fast.cu", "modes_impl.cuh", "modes.cuh", "zfft_impl.cuh"],
+    "mode_z": ["modes_z.cu", "modes_impl.cuh", "modes.cuh", "zfft_impl.cuh", "fft_common.cuh"],
+    "mode_back": ["modes_fast.cu", "modes_impl.cuh", "modes.cuh", "zfft_impl.cuh"],
 }
 PROFILE_FILES = {
     "transverse": "transverse_dsts_pipe128x128x1024_igf_f32.md",

@@ -71,12 +71,13 @@ cudaError_t launch_pb2(int which, bool fy, const ModeArgs<T>& a, cudaStream_t st
 // 256 threads per CTA, L/4 per column (L = nz in 32..1024)
 template <typename T>
 cudaError_t launch_zc(const ModeArgs<T>& a, cudaStream_t st) {
+  const int xblocks = a.nx / ModeShape<T>::XB;
+  if constexpr (sizeof(T) == 4) return launch_mode_z_warp(a, xblocks / mode_cluster(xblocks), st);
   const int per = 1024 / a.nz;                       // columns per CTA
   const size_t smem = sizeof(C2<T>) * (size_t(per) * 2 * a.nz + 3 * size_t(a.nz));
   void (*kern)(ModeArgs<T>, int) = mode_z_kernel<T>;
   cudaError_t e;
   if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
-  const int xblocks = a.nx / ModeShape<T>::XB;
   kern<<<(a.mc + per - 1) / per, 256, smem, st>>>(a, xblocks / mode_cluster(xblocks));
   return cudaGetLastError();
 }

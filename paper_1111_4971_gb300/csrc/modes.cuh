@@ -74,6 +74,10 @@ inline int mode_cluster(int xblocks) {
 template <typename T>
 cudaError_t launch_mode_stage(int stage, int myp, bool fy, const ModeArgs<T>& a, cudaStream_t st);
 
+// the FP32 z convolution, one warp-level FFT per mode column (modes_z.cu):
+// nz in 32..1024, groups partial projections summed on load
+cudaError_t launch_mode_z_warp(const ModeArgs<float>& a, int groups, cudaStream_t st);
+
 // the FP32 projection and back-projection laid out for occupancy
 // (modes_fast.cu): meshes symmetric in y with ny/2 in {16, 32, 64}
 bool mode_fast_ok(int ny, int nx, int myp, bool fy);
