@@ -239,8 +239,54 @@ static cudaError_t octant_transform(double* T, double* tmp, double* cosbuf, int 
   return cudaMemcpyAsync(T, tmp, sizeof(double) * sz * (nz + 1), cudaMemcpyDeviceToDevice, st);
 }
 
+cudaError_t build_pipe_spectrum_from_modes(const GreenSpec& s, double* g64, float* g32, cudaStream_t st,
+                                           bool transform_z);
+__global__ void z_dct_kernel(double* Zh, const double* Z, int MN, int nz, const double* cosn);
+
+// The octant's x-y transform straight from the modes.  The table is
+// T[r][q][p] = C sum_mn cos(pi m p / nx) cos(pi n q / ny) Z_mn(r) (a mesh that
+// spans the pipe: nx hx = a), and the weighted DCT-I of cos(pi m p / n) over
+// p = 0..n is n delta(k - m'), m' the alias of m in [0, n] (m mod 2n, or
+// 2n - (m mod 2n) above n), 2n delta at the end points k = 0 and k = n.  So
+//   T^[r][ky][kx] = C sum over the modes m aliasing to kx and n aliasing to ky
+//                   of dx dy Zs[m][n][r],
+// Zs the z profiles (banded tables) or their DCT-I along z (full solve).
+// Candidates for k: m = k + 2nj (j >= 0) and m = 2nj - k (j >= 1; the same
+// modes again when k = 0 or n).
+__global__ void octant_from_modes_kernel(double* T, const double* Zs, int M, int N, int nx, int ny, int nz,
+                                         double C) {
+  const long idx = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long total = long(nx + 1) * (ny + 1) * (nz + 1);
+  if (idx >= total) return;
+  const int p = int(idx % (nx + 1));
+  const int q = int((idx / (nx + 1)) % (ny + 1));
+  const int r = int(idx / (long(nx + 1) * (ny + 1)));
+  const double dx = (p == 0 || p == nx) ? 2.0 * nx : double(nx);
+  const double dy = (q == 0 || q == ny) ? 2.0 * ny : double(ny);
+  double acc = 0.0;
+#pragma unroll 1
+  for (int fm = 0; fm < 2; ++fm) {
+    if (fm == 1 && (p == 0 || p == nx)) break;
+#pragma unroll 1
+    for (int m = fm == 0 ? p : 2 * nx - p; m <= M; m += 2 * nx) {
+      if (m < 1) continue;
+#pragma unroll 1
+      for (int fn = 0; fn < 2; ++fn) {
+        if (fn == 1 && (q == 0 || q == ny)) break;
+#pragma unroll 1
+        for (int n = fn == 0 ? q : 2 * ny - q; n <= N; n += 2 * ny) {
+          if (n < 1) continue;
+          acc += Zs[(long(m - 1) * N + (n - 1)) * (nz + 1) + r];
+        }
+      }
+    }
+  }
+  T[idx] = C * dx * dy * acc;
+}
+
 cudaError_t build_pipe_spectrum(const GreenSpec& s, double* g64, float* g32, cudaStream_t st,
                                 bool transform_z) {
+  if (s.modes_m <= 64 && s.modes_n <= 64) return build_pipe_spectrum_from_modes(s, g64, g32, st, transform_z);
   const int nx = s.nx, ny = s.ny, nz = s.nz, M = s.modes_m, N = s.modes_n;
   const long oct = long(nx + 1) * (ny + 1) * (nz + 1);
   double *cx = nullptr, *cy = nullptr, *Z = nullptr, *U = nullptr, *T = nullptr, *tmp = nullptr,
@@ -269,6 +315,33 @@ cudaError_t build_pipe_spectrum(const GreenSpec& s, double* g64, float* g32, cud
   err = cudaStreamSynchronize(st);
 done:
   cudaFree(cx); cudaFree(cy); cudaFree(Z); cudaFree(U); cudaFree(T); cudaFree(tmp); cudaFree(cosbuf);
+  return err;
+}
+
+// build_pipe_spectrum for up to 64 modes per axis: z profiles, their DCT-I
+// along z per mode (full solve), the octant gathered from the modes, scaled.
+cudaError_t build_pipe_spectrum_from_modes(const GreenSpec& s, double* g64, float* g32, cudaStream_t st,
+                                           bool transform_z) {
+  const int nx = s.nx, ny = s.ny, nz = s.nz, M = s.modes_m, N = s.modes_n;
+  const long oct = long(nx + 1) * (ny + 1) * (nz + 1);
+  double *Z = nullptr, *Zh = nullptr, *T = nullptr, *cosn = nullptr;
+  cudaError_t err = cudaSuccess;
+  if ((err = cudaMalloc(&Z, sizeof(double) * size_t(M) * N * (nz + 1))) != cudaSuccess) goto done;
+  if ((err = cudaMalloc(&T, sizeof(double) * oct)) != cudaSuccess) goto done;
+  z_profile_kernel<<<nblk(long(M) * N * (nz + 1), 256), 256, 0, st>>>(Z, M, N, nz, s.hz, s.a, s.b, s.igf);
+  if (transform_z) {
+    if ((err = cudaMalloc(&Zh, sizeof(double) * size_t(M) * N * (nz + 1))) != cudaSuccess) goto done;
+    if ((err = cudaMalloc(&cosn, sizeof(double) * 2 * nz)) != cudaSuccess) goto done;
+    cos_pi_table_kernel<<<nblk(2 * nz, 256), 256, 0, st>>>(cosn, nz);
+    z_dct_kernel<<<nblk(long(M) * N * (nz + 1), 256), 256, 0, st>>>(Zh, Z, M * N, nz, cosn);
+  }
+  octant_from_modes_kernel<<<nblk(oct, 256), 256, 0, st>>>(T, transform_z ? Zh : Z, M, N, nx, ny, nz,
+                                                           2.0 * M_PI / (s.a * s.b));
+  finalize_kernel<<<nblk(oct, 256), 256, 0, st>>>(T, g64, g32, oct, s.scale);
+  if ((err = cudaGetLastError()) != cudaSuccess) goto done;
+  err = cudaStreamSynchronize(st);
+done:
+  cudaFree(Z); cudaFree(Zh); cudaFree(T); cudaFree(cosn);
   return err;
 }
 
