@@ -126,6 +126,7 @@ void free_handle(pipe_handle* h) {
   cudaFree(h->msx64); cudaFree(h->msy64); cudaFree(h->mgz64);
   cudaFree(h->msx32); cudaFree(h->msy32); cudaFree(h->mgz32);
   cudaFree(h->mwork);
+  cudaFree(h->mkb64); cudaFree(h->mkb32);
   std::free(h->msy_host);
   for (int k = 0; k < 2; ++k) {
     cudaFree(h->ring_rho[k]);
@@ -212,10 +213,10 @@ int run_solve(pipe_handle* h, const void* rho, void* phi, bool adjoint, cudaStre
   h->inject_drop = 0;
   h->inject_polls = 0;
   cudaError_t e;
-  // the banded operator is symmetric: the adjoint is the same computation
-  if (h->banded >= 0) return status_of(launch_banded<T>(h->plan.t_threads, a, h->banded, st));
-  // so is the mode-space form of the full operator
+  // the banded operator is symmetric: the adjoint is the same computation;
+  // so is the mode-space form (full or banded)
   if (h->use_modes) return mode_solve(h, rho, phi, h->mwork, st);
+  if (h->banded >= 0) return status_of(launch_banded<T>(h->plan.t_threads, a, h->banded, st));
   if constexpr (std::is_same<T, float>::value) {
     if (h->grid.dtype == PIPE_F32_C16) {
       const int zw = h->plan.z_warps;
@@ -269,6 +270,8 @@ ModeArgs<T> mode_args(const pipe_handle* h, const void* rho, void* phi, void* pa
   a.mx = h->geom.modes_m;
   a.mxp = h->mxp;
   a.mc = h->mxp * h->myp;
+  a.kb = reinterpret_cast<const T*>(D ? static_cast<const void*>(h->mkb64) : static_cast<const void*>(h->mkb32));
+  a.nb = h->banded;
   return a;
 }
 
@@ -351,9 +354,9 @@ static int setup_pipe(const pipe_geometry* geom, const pipe_grid* grid, int igf,
   if (geom->y0 + (grid->ny - 1) * grid->hy > geom->b * (1 + tol)) return PIPE_EINVAL;
   // the mode-space form (modes_impl.cuh): any mesh inside the pipe with
   // nx, ny multiples of 16 (up to 4096), nz a power of two in 32..1024 and at
-  // most 32 modes per axis, FP32 or FP64, full operator (not banded)
+  // most 32 modes per axis, FP32 or FP64, full or banded operator
   const bool fold = std::fabs(2.0 * geom->y0 + (grid->ny - 1) * grid->hy - geom->b) <= 1e-12 * geom->b;
-  bool modes_ok = n_nb < 0 && (grid->dtype == PIPE_F32 || grid->dtype == PIPE_F64) &&
+  bool modes_ok = n_nb < grid->nz && (grid->dtype == PIPE_F32 || grid->dtype == PIPE_F64) &&
                   grid->nx % 16 == 0 && grid->ny % 16 == 0 && grid->nx <= 4096 && grid->ny <= 4096 &&
                   is_pow2(grid->nz) && grid->nz >= 32 && grid->nz <= 1024 && geom->modes_m <= 32 &&
                   mode_slots(geom->modes_n, fold) > 0;
@@ -384,11 +387,14 @@ static int setup_pipe(const pipe_geometry* geom, const pipe_grid* grid, int igf,
 
   if (grid->dtype == PIPE_F32_C16 && (sx != 1 || sy != 1 || n_nb >= 0)) return PIPE_EUNSUPPORTED;
   if (n_nb >= 0) {
-    // the banded form: n-point transverse routine (cell-centred meshes), planes
-    // paired along z, the nx*ny plane buffer in shared memory
+    // the banded form: in mode space (a stencil on each mode column) where the
+    // mode form takes the mesh; its transform form takes cell-centred meshes
+    // (n-point transverse routine, planes paired along z, the nx*ny plane
+    // buffer in shared memory)
     if (n_nb >= grid->nz) return PIPE_EINVAL;
-    if (sx != 1 || sy != 1) return PIPE_EUNSUPPORTED;
-    if (cplx_size(grid->dtype) * grid->nx * grid->ny > 200 * 1024) return PIPE_EUNSUPPORTED;
+    if (st == PIPE_OK && (sx != 1 || sy != 1 || cplx_size(grid->dtype) * grid->nx * grid->ny > 200 * 1024))
+      st = PIPE_EUNSUPPORTED;
+    if (st != PIPE_OK && !modes_ok) return st;
   }
   const bool fft_ok = st == PIPE_OK;
   int ndev = 0;
@@ -436,6 +442,17 @@ static int setup_pipe(const pipe_geometry* geom, const pipe_grid* grid, int igf,
     cudaError_t e = build_mode_tables(s, geom->x0, geom->y0, h->mxp, h->myp, h->fy, h->msx64, h->msx32,
                                       h->msy64, h->msy32, h->mgz64, h->mgz32, nullptr);
     if (e != cudaSuccess) { free_handle(h); return status_of(e); }
+    if (n_nb >= 0) {                     // the banded operator's z stencil
+      const size_t nkb = size_t(h->mxp) * h->myp * (n_nb + 1);
+      if (cudaMalloc(&h->mkb64, nkb * 8) != cudaSuccess || cudaMalloc(&h->mkb32, nkb * 4) != cudaSuccess) {
+        free_handle(h);
+        return PIPE_ENOMEM;
+      }
+      if ((e = build_mode_band(s, h->mxp, h->myp, h->fy, n_nb, h->mkb64, h->mkb32, nullptr)) != cudaSuccess) {
+        free_handle(h);
+        return status_of(e);
+      }
+    }
     if (grid->dtype == PIPE_F32 && mode_fast_ok(grid->ny, grid->nx, h->myp, fold)) {
       h->msy_host = static_cast<float*>(std::malloc(nsy * sizeof(float)));
       if (!h->msy_host) { free_handle(h); return PIPE_ENOMEM; }

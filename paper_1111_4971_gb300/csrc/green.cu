@@ -518,6 +518,35 @@ __global__ void mode_gz_kernel(double* g64, float* g32, const double* Zh, int M,
   g32[idx] = float(v);
 }
 
+// kb[c][d] = hx hy hz (8 pi / ab) kappa^{-1} f_mn(d hz), d = 0..nb, c = (m-1) myp + slot(n):
+// the real-space z kernel of the banded operator in the mode slots
+__global__ void mode_kb_kernel(double* k64, float* k32, const double* Z, int M, int N, int mxp, int myp,
+                               int fold, int nb, double C) {
+  const long idx = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= long(mxp) * myp * (nb + 1)) return;
+  const int d = int(idx % (nb + 1));
+  const int c = int(idx / (nb + 1));
+  const int m = c / myp + 1, s = c % myp;
+  const int n = !fold ? s + 1 : (s < myp / 2 ? 2 * s + 1 : 2 * (s - myp / 2) + 2);
+  const double v = (m <= M && n <= N) ? C * Z[(long(m - 1) * N + (n - 1)) * (nb + 1) + d] : 0.0;
+  k64[idx] = v;
+  k32[idx] = float(v);
+}
+
+cudaError_t build_mode_band(const GreenSpec& s, int mxp, int myp, int fold, int nb, double* kb64, float* kb32,
+                            cudaStream_t st) {
+  const int M = s.modes_m, N = s.modes_n;
+  double* Z = nullptr;
+  cudaError_t err = cudaMalloc(&Z, sizeof(double) * size_t(M) * N * (nb + 1));
+  if (err != cudaSuccess) return err;
+  z_profile_kernel<<<nblk(long(M) * N * (nb + 1), 256), 256, 0, st>>>(Z, M, N, nb, s.hz, s.a, s.b, s.igf);
+  mode_kb_kernel<<<nblk(long(mxp) * myp * (nb + 1), 256), 256, 0, st>>>(
+      kb64, kb32, Z, M, N, mxp, myp, fold, nb, s.hx * s.hy * s.hz * 8.0 * M_PI / (s.a * s.b));
+  if ((err = cudaGetLastError()) == cudaSuccess) err = cudaStreamSynchronize(st);
+  cudaFree(Z);
+  return err;
+}
+
 cudaError_t build_mode_tables(const GreenSpec& s, double x0, double y0, int mxp, int myp, int fold,
                               double* sx64, float* sx32, double* sy64, float* sy32, double* gz64,
                               float* gz32, cudaStream_t st) {

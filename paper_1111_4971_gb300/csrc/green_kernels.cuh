@@ -38,6 +38,11 @@ cudaError_t build_free_spectrum(const GreenSpec& s, double self_value, double* g
 // Tables of the mode-space solve: FP64 and FP32 copies of sx [nx][mxp],
 // sy [fold ? ny/2 : ny][myp] and gz [mxp*myp][nz+1] (see green.cu).
 // Synchronous on `st`.  Uses temporary device memory (freed before return).
+// The banded operator's real-space z kernel in the mode slots, kb [mxp*myp][nb+1]
+// (FP64 and FP32).  Synchronous on `st`.  Uses temporary device memory.
+cudaError_t build_mode_band(const GreenSpec& s, int mxp, int myp, int fold, int nb, double* kb64, float* kb32,
+                            cudaStream_t st);
+
 cudaError_t build_mode_tables(const GreenSpec& s, double x0, double y0, int mxp, int myp, int fold,
                               double* sx64, float* sx32, double* sy64, float* sy32, double* gz64,
                               float* gz32, cudaStream_t st);

@@ -59,6 +59,8 @@ struct pipe_handle {
   int mxp = 0, myp = 0, fy = 0;
   double *msx64 = nullptr, *msy64 = nullptr, *mgz64 = nullptr;
   float *msx32 = nullptr, *msy32 = nullptr, *mgz32 = nullptr;
+  double* mkb64 = nullptr;     // banded operator in mode space: [mxp*myp][nb+1] real-space z kernel
+  float* mkb32 = nullptr;
   void* mwork = nullptr;       // part [xblocks][mc][nz], then psi [mc][nz], of the dtype
   float* msy_host = nullptr;   // FP32 y-mode table in host memory (the projection's kernel parameter)
   int mfast = 0;               // FP32 projection / back-projection in their occupancy layout

@@ -23,7 +23,51 @@ __global__ void __launch_bounds__(256) mode_z_kernel(ModeArgs<T> a, int groups) 
   mode_z<T>(a, groups, smem_raw);
 }
 
+// Banded z stage (Sec. 5, Eq. 17-18 in mode space): psi[c][k] =
+// sum_{|d| <= nb, 0 <= k-d < nz} K_c(|d|) rhot[c][k-d], rhot the groups' partial
+// projections summed.  One CTA per column: the column (zero-padded by nb on
+// both sides) and its taps in shared memory, taps summed from d = -nb up.
+constexpr int kBandThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kBandThreads) mode_band_kernel(ModeArgs<T> a, int groups) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* win = reinterpret_cast<T*>(smem_raw);           // [nz + 2 nb]: win[nb + k] = rhot[k]
+  T* taps = win + a.nz + 2 * a.nb;                   // [nb + 1]
+  const int c = int(blockIdx.x);
+  const int nw = a.nz + 2 * a.nb;
+  for (int i = int(threadIdx.x); i < nw; i += kBandThreads) {
+    const int k = i - a.nb;
+    T v = T(0);
+    if (k >= 0 && k < a.nz)
+      for (int s = 0; s < groups; ++s) v += a.part[(size_t(s) * a.mc + c) * a.nz + k];
+    win[i] = v;
+  }
+  for (int d = int(threadIdx.x); d <= a.nb; d += kBandThreads) taps[d] = a.kb[size_t(c) * (a.nb + 1) + d];
+  __syncthreads();
+  for (int k = int(threadIdx.x); k < a.nz; k += kBandThreads) {
+    const T* w = win + k + a.nb;                     // w[-d] = rhot[k - d]
+    T acc = T(0);
+    for (int d = -a.nb; d <= a.nb; ++d) acc += taps[d < 0 ? -d : d] * w[-d];
+    a.psi[size_t(c) * a.nz + k] = acc;
+  }
+}
+
 namespace {
+
+template <typename T>
+cudaError_t launch_band(const ModeArgs<T>& a, cudaStream_t st) {
+  const int xblocks = a.nx / ModeShape<T>::XB;
+  const size_t smem = sizeof(T) * (size_t(a.nz) + 3 * size_t(a.nb) + 1);
+  void (*kern)(ModeArgs<T>, int) = mode_band_kernel<T>;
+  if (smem > 48 * 1024) {
+    if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<unsigned(a.mc), kBandThreads, smem, st>>>(a, xblocks / mode_cluster(xblocks));
+  return cudaGetLastError();
+}
 
 template <typename K>
 cudaError_t set_smem(K kern, size_t smem) {
@@ -94,6 +138,7 @@ cudaError_t launch_mode_stage<PP_M_TYPE>(int stage, int myp, bool fy, const Mode
   using T = PP_M_TYPE;
   if (stage == 1) {
     if (a.nz < 32 || a.nz > 1024 || (a.nz & (a.nz - 1))) return cudaErrorInvalidValue;
+    if (a.nb >= 0) return launch_band<T>(a, st);
     return launch_zc<T>(a, st);
   }
   const int which = stage == 0 ? 0 : 1;

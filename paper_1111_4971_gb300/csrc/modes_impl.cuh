@@ -66,6 +66,8 @@ struct ModeArgs {
   int mx;                // x modes
   int mxp;               // x modes padded to a multiple of 4 (columns of sx)
   int mc;                // mxp * MYP mode columns
+  const T* kb;           // banded operator: [mc][nb+1] real-space z kernel K_c(d), d = 0..nb
+  int nb;                // neighbour planes of the banded operator (Eq. 18), -1: the full z convolution
 };
 
 template <typename T, int MYP, bool FY>

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from inputs.bunches import cell_centred, gaussian_bunch, random_density
+from inputs.bunches import Geometry, Grid, cell_centred, gaussian_bunch, random_density
 from oracle import pipe
 from test_gpu_parity import F32_TOL, F64_TOL, dev, host, rel
 
@@ -109,8 +109,50 @@ def test_banded_handle_refused_by_other_entry_points():
     rho = dev(random_density(grid.shape, 1), torch.float32)
     with pytest.raises(PipeError):
         solve_batched([s, other], [rho, rho], [s.empty(), other.empty()])
-    wall = (type(geom)(geom.a, geom.b, 0.0, 0.0, 20, 20), grid)
-    with pytest.raises(PipeError):
-        solver(*wall, 1, 1, torch.float32)
     with pytest.raises(PipeError):
         solver(geom, grid, 1, grid.nz, torch.float32)
+    # a banded handle the mode form cannot take either (more than 32 modes on a
+    # wall-node mesh, which the banded transform kernels do not take)
+    with pytest.raises(PipeError):
+        solver(type(geom)(geom.a, geom.b, 0.0, 0.0, 40, 40), grid, 1, 1, torch.float32)
+
+
+# the banded operator in mode space (plan t_kind 3): projection, a
+# (2 n_nb + 1)-tap stencil on each mode column, back-projection
+MODE_CASES = dict(CASES)
+# node on the wall, unequal mode counts: only the mode form takes it
+MODE_CASES["wall32x16x64"] = (Geometry(1.0, 0.5, 0.0, 0.0, 12, 9), Grid(32, 16, 64, 1 / 32, 0.5 / 16, 0.05))
+# nx != ny, not a power of two
+MODE_CASES["cc48x32x64"] = cell_centred(1.5, 1.0, 48, 32, 64, 0.05, modes=16)
+
+
+@pytest.mark.parametrize("n_nb", [0, 1, 3])
+@pytest.mark.parametrize("key", list(MODE_CASES))
+def test_banded_mode_form_against_oracle(key, n_nb):
+    geom, grid = MODE_CASES[key]
+    rho = random_density(grid.shape, 500 + n_nb, sparsity=0.3)
+    for igf in (0, 1):
+        want = pipe.banded_solve(rho, geom, grid, igf, n_nb)
+        for dtype, tol in ((torch.float64, F64_TOL), (torch.float32, F32_TOL)):
+            s = solver(geom, grid, igf, n_nb, dtype)
+            if s.plan["t_kind"] != 3:
+                s.set_plan(t_kind=3)
+            assert s.plan["t_kind"] == 3
+            got = host(s.solve(dev(rho, dtype)))
+            assert rel(got, want) <= tol, (igf, dtype, rel(got, want))
+            # symmetric operator: the adjoint is the same computation
+            assert torch.equal(s.adjoint(dev(rho, dtype)), s.solve(dev(rho, dtype)))
+
+
+def test_banded_mode_form_full_band_and_default():
+    """The band covering every plane is the full operator; on 64^2 and wider
+    planes (modes at most half the mesh) the mode form is the banded default."""
+    from paper_1111_4971_gb300 import PipeSolver
+    geom, grid = MODE_CASES["cc48x32x64"]
+    rho = random_density(grid.shape, 44)
+    full = host(PipeSolver(geom, grid, igf=True, dtype=torch.float64).solve(dev(rho, torch.float64)))
+    s = solver(geom, grid, 1, grid.nz - 1, torch.float64)
+    assert s.plan["t_kind"] == 3
+    assert rel(host(s.solve(dev(rho, torch.float64))), full) <= F64_TOL
+    g64, gr64 = CASES["rect64x64x32"]
+    assert solver(g64, gr64, 1, 2, torch.float32).plan["t_kind"] == 3
