@@ -117,6 +117,39 @@ def mode_alg_bytes(nx, ny, nz, mc, groups, esz=4):
             "mode_back": psi + field}
 
 
+def mode_flops(nx, ny, nz, mx, mxp, myp, fold, mc):
+    """Floating-point operations per launch of the mode-space kernels, counted
+    from their sums (an FMA is 2): the projection's y sums (over ny/2 folded
+    pairs, or ny rows) and x sums, the back-projection's x sums and y sums, and
+    for the z kernel two complex L = nz point FFTs per column at 5 L log2 L
+    plus the spectral product (about 40 flops per point)."""
+    import math
+    yrows = ny // 2 if fold else ny
+    proj = 2 * nx * nz * myp * (yrows + mxp) + (2 * nx * nz * yrows if fold else 0)
+    back = 2 * nx * nz * myp * (mx + yrows) + (2 * nx * nz * yrows if fold else 0)
+    zc = mc * (2 * 5 * nz * int(math.log2(nz)) + 40 * nz)
+    return {"mode_project": proj, "mode_z": zc, "mode_back": back}
+
+
+def dgemm_tflops(n=4096, reps=3):
+    """Measured dense FP64 rate of this GPU: a cuBLAS DGEMM (torch.matmul on
+    float64), as the yardstick of the FP64 path's arithmetic rate."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (min(ts) * 1e-3) / 1e12
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if still current."""
     path = os.path.join(ROOT, "profiles", PROFILE_FILES[kernel])
@@ -456,13 +489,20 @@ def run_ours(args):
         s32.solve(rho, phi)
     barrier(world)
     if args.solves_only:                       # profiling target: K plain solves
+        sp, rp, pp_ = s32, rho, phi
+        if args.dtype == "f64":
+            sp = PipeSolver(geom, grid, igf=True, dtype=torch.float64)
+            rp = rho.double()
+            pp_ = sp.empty()
+            for _ in range(args.warmup):
+                sp.solve(rp, pp_)
         for _ in range(args.steps):
             if args.flush:
                 flush.fill_(0.0)
-            s32.solve(rho, phi)
+            sp.solve(rp, pp_)
         barrier(world)
         if rank == 0:
-            print(json.dumps({"solves_only": args.steps, "plan": s32.plan}))
+            print(json.dumps({"solves_only": args.steps, "plan": sp.plan, "dtype": args.dtype}))
         return 0
 
     sampler = ClockSampler(local)
@@ -653,6 +693,26 @@ def run_ours(args):
                                 "rel_l2_vs_fp64": float(np.linalg.norm(p16 - p64) / np.linalg.norm(p64))}
         line["fp64"] = {"solves_per_s": 1e3 / statistics.median(t64), "ms": statistics.median(t64),
                         "plan": s64.plan}
+        if s64.plan["t_kind"] == 3:
+            # the FP64 mode kernels against the measured FP64 rate: they run
+            # on the FP64 FMA units, so their bound is arithmetic, not HBM
+            m64 = s64.mode_layout()
+            part64, psi64 = s64.mode_buffers()
+            st64 = [lambda: s64.stage_modes(0, rho64, part64), lambda: s64.stage_modes(1, part64, psi64),
+                    lambda: s64.stage_modes(2, psi64, phi64)]
+            k64 = time_stages(st64, stage_names, 5, flush, stream)
+            k64 = {k: statistics.median(v) for k, v in k64.items()}
+            fl = mode_flops(nx, ny, nz, m64[0], m64[1], m64[2], m64[3], m64[1] * m64[2])
+            peak64 = dgemm_tflops()
+            rate = {k: fl[k] / (k64[k] * 1e-3) / 1e12 for k in k64}
+            dom64 = max(k64, key=k64.get)
+            line["fp64"].update({
+                "kernels_ms": k64, "kernels_flops": fl, "kernels_tflops": rate,
+                "peak_tflops": peak64, "peak_kind": "measured: cuBLAS DGEMM 4096^3 (torch.matmul)",
+                "roofline": {"bound": "fp64", "kernel": dom64, "achieved": rate[dom64], "peak": peak64,
+                             "unit": "TFLOP/s", "frac": rate[dom64] / peak64},
+                "solve_tflops": sum(fl.values()) / (statistics.median(t64) * 1e-3) / 1e12,
+                "solve_frac": sum(fl.values()) / (statistics.median(t64) * 1e-3) / 1e12 / peak64})
         # the FP64 padded-transform form (n-point transverse routine, global scratch planes)
         s64t = PipeSolver(geom, grid, igf=True, dtype=torch.float64)
         s64t.set_plan(z_warps=8, z_pipe=0, t_h=1, t_threads=256, t_kind=1)
@@ -708,6 +768,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the FP64 / Hockney extras")
     ap.add_argument("--check-oracle", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"],
+                    help="with --solves-only: the solves' dtype (profiling of the FP64 kernels)")
     ap.add_argument("--form", default="default", choices=["default", "transforms"],
                     help="transforms: time the padded-transform form (profiling of its kernels)")
     ap.add_argument("--solves-only", action="store_true",
