@@ -438,7 +438,7 @@ def bench_banded(args):
     t_full = timed(full, pf)
     ref = pf.double()
     out = {"workload": "pipe128x128x1024_igf_sigmaz30a", "full_ms": t_full, "bands": []}
-    for nb in (0, 2, 8, 16):
+    for nb in (0, 2, 8, 10, 16):
         s = PipeSolver(geom, grid, igf=True, dtype=torch.float32, banded=nb)
         p = s.empty()
         t = timed(s, p)
@@ -583,8 +583,10 @@ def run_ours(args):
         "kernels_gbs": achieved,
         # what the memory delivers for the field's 64 MB under the same flush
         # (plain read / write, library kernels): the floors of the projection
-        # and the back-projection
-        "memory_floors": floors,
+        # and the back-projection, and each kernel's time against its floor
+        "memory_floors": dict(floors, **({
+            "mode_project_floor_over_kernel": floors["read_field_ms"] / means["mode_project"],
+            "mode_back_floor_over_kernel": floors["write_field_ms"] / means["mode_back"]} if modes_form else {})),
         "kernels_source_sha256": {k: source_hash(k) for k in KERNEL_SOURCES},
         # the whole solve against its own algorithmic bytes (the sum over its kernels)
         "solve_alg_bytes": solve_bytes,
