@@ -132,17 +132,24 @@ int pipe_green_setup(const pipe_geometry* geometry, const pipe_grid* grid, int i
  * plane).  Accurate when the Green function (usually the IGF on a z mesh
  * coarse against the pipe width) is negligible beyond n_neighbors planes;
  * n_neighbors = nz - 1 reproduces the full solve.  No transform along z is
- * taken: the 2-D spectra of the tables at offsets 0..n_neighbors are computed
- * once (FP64) and the solve is two kernels over pairs of z planes.
+ * taken.  Two forms, chosen like the full solve's (pipe_get_plan t_kind 3 or
+ * not):
+ *   mode space (any mesh the mode-space form of pipe_green_setup takes): the
+ *     projection onto the modes, a (2 n_neighbors + 1)-tap stencil along z on
+ *     each mode column with the real-space kernel K_mn(d hz), d <= n_neighbors
+ *     (FP64 tables, FP32 copy), and the back-projection; pipe_stage_modes
+ *     stage 1 runs the stencil;
+ *   transforms (cell-centred meshes, 2*x0/hx == 2*y0/hy == 1, with an nx*ny
+ *     complex plane of at most 200 KB: FP32 up to 128^2, FP64 up to 64^2):
+ *     the 2-D spectra of the tables at offsets 0..n_neighbors, computed once
+ *     (FP64), and two kernels over pairs of z planes; pipe_green_spectrum
+ *     returns its (nx+1)*(ny+1)*(n_neighbors+1) planes [d][ky][kx], scaled
+ *     by hx*hy*hz/(4*nx*ny).
  * pipe_poisson_solve and pipe_poisson_adjoint (the same operator: it is
- * symmetric) and pipe_poisson_solve_host accept the handle; the stage,
- * no-alloc and batched entry points return PIPE_EUNSUPPORTED for it.
- * Requirements beyond pipe_green_setup's: cell-centred mesh (2*x0/hx ==
- * 2*y0/hy == 1) and an nx*ny complex plane of at most 200 KB (FP32 up to
- * 128^2, FP64 up to 64^2).  pipe_green_spectrum returns its
- * (nx+1)*(ny+1)*(n_neighbors+1) planes [d][ky][kx], scaled by
- * hx*hy*hz/(4*nx*ny).  Errors: as pipe_green_setup, plus PIPE_EINVAL for
- * n_neighbors < 0 or >= nz. */
+ * symmetric) and pipe_poisson_solve_host accept the handle; the transform
+ * stage, no-alloc and batched entry points return PIPE_EUNSUPPORTED for it.
+ * Errors: as pipe_green_setup (PIPE_EUNSUPPORTED when neither form takes the
+ * mesh), plus PIPE_EINVAL for n_neighbors < 0 or >= nz. */
 int pipe_banded_setup(const pipe_geometry* geometry, const pipe_grid* grid, int igf, int n_neighbors,
                       pipe_handle** out);
 
@@ -332,7 +339,9 @@ int pipe_mode_spectrum(pipe_handle* h, double* out, size_t count);
  *                            sin(n pi y_j/b) rho[i][j][k]
  *   stage 1: in = part -> out = psi [mxp*myp][nz]: the blocks summed, each
  *            column convolved along z with its kernel (zero-padded 2nz-point
- *            transforms, the spectrum of pipe_mode_spectrum), first nz values
+ *            transforms, the spectrum of pipe_mode_spectrum), first nz values;
+ *            for a banded handle (pipe_banded_setup) the sum over
+ *            |d| <= n_neighbors of K_c(|d| hz) part[c][k - d] instead
  *   stage 2: in = psi -> out = phi [nx][ny][nz]:
  *            phi[i][j][k] = sum_{m,n} sin(m pi x_i/a) sin(n pi y_j/b) psi[c][k]
  * The three in a row are the solve of this form (pipe_poisson_solve with plan
