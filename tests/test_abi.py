@@ -123,8 +123,12 @@ def test_banded_setup_validation_without_gpu(L):
     cases = [
         (cc, good, -1, _lib.PIPE_EINVAL),                                  # negative band
         (cc, good, 256, _lib.PIPE_EINVAL),                                 # band >= nz
-        (G(1.0, 1.0, 0.0, 0.0, 20, 20), good, 1, _lib.PIPE_EUNSUPPORTED),  # x0 = 0: s = 0
-        (cc, P(128, 128, 256, 1 / 128, 1 / 128, 0.1, 1), 1, _lib.PIPE_EUNSUPPORTED),  # FP64 128^2
+        # meshes neither banded form takes: more than 32 modes (beyond the
+        # mode-space form) with x0 = 0 (s = 0) or an FP64 128^2 plane (beyond
+        # the banded transform kernels)
+        (G(1.0, 1.0, 0.0, 0.0, 40, 40), good, 1, _lib.PIPE_EUNSUPPORTED),
+        (G(1.0, 1.0, 0.5 / 128, 0.5 / 128, 40, 40), P(128, 128, 256, 1 / 128, 1 / 128, 0.1, 1), 1,
+         _lib.PIPE_EUNSUPPORTED),
     ]
     for geo, grid, n_nb, want in cases:
         h = ctypes.c_void_p()
