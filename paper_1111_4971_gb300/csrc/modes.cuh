@@ -19,16 +19,28 @@ struct ModeShape {
   static constexpr int YK = 4;                               // y rows per stage (and their mirrors)
   static constexpr int STAGES = 3;
   static constexpr int MQ = sizeof(T) == 4 ? 4 : 2;          // x modes per pass of the projection
+  // the projection's x modes in this many rounds, each summed over the
+  // cluster before the next: the block's projection buffer holds one round
+  // (FP64: half the modes, so that two CTAs fit in an SM's shared memory)
+  static constexpr int RED_PASSES = sizeof(T) == 4 ? 1 : 2;
 };
 
+// x modes of one round of the projection (a multiple of MQ)
+template <typename T>
+__host__ __device__ inline int mode_round_modes(int mxp) {
+  using S = ModeShape<T>;
+  return (mxp + S::RED_PASSES * S::MQ - 1) / (S::RED_PASSES * S::MQ) * S::MQ;
+}
+
 // shared memory of the projection (elements): the ring of row stages, which
-// after the y loop holds the y-mode sums [XB][myp][ZC] and the block's
-// projection [mxp * myp][ZC]; then the y-mode table and the block's x rows
+// after the y loop holds the y-mode sums [XB][myp][ZC] and one round of the
+// block's projection [mode_round_modes * myp][ZC]; then the y-mode table and
+// the block's x rows
 template <typename T>
 __host__ __device__ inline size_t mode_proj_union(int mxp, int myp, bool fy) {
   using S = ModeShape<T>;
   const size_t slab = size_t(S::STAGES) * S::XB * (fy ? 2 * S::YK : S::YK) * S::ZC;
-  const size_t after = size_t(S::XB) * myp * S::ZC + size_t(mxp) * myp * S::ZC;
+  const size_t after = size_t(S::XB) * myp * S::ZC + size_t(mode_round_modes<T>(mxp)) * myp * S::ZC;
   return slab > after ? slab : after;
 }
 template <typename T>

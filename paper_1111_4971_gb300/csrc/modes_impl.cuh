@@ -108,7 +108,7 @@ __device__ __forceinline__ void mode_project(const ModeArgs<T>& a, unsigned char
   static_assert(MYP % 4 == 0, "mode slots in fours");
   T* slab = reinterpret_cast<T*>(smem_raw);
   T* abuf = slab;                                   // once the slab is consumed
-  T* red = abuf + Cfg::ABUF;                        // the block's projection [mc][ZC]
+  T* red = abuf + Cfg::ABUF;                        // one round of the block's projection [.][ZC]
   T* sy = slab + Cfg::union_elems(a.mxp);
   T* sxs = sy + (FY ? a.ny / 2 : a.ny) * MYP;       // x-mode rows of the block [XB][mxp]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -192,48 +192,54 @@ __device__ __forceinline__ void mode_project(const ModeArgs<T>& a, unsigned char
     for (int n = 0; n < MYP; ++n) abuf[((warp * S::XPW + i) * MYP + n) * S::ZC + lane] = acc[i][n];
   __syncthreads();
 
-  // x modes: warp w takes the passes of MQ modes q = w, w + WARPS, ...
-#pragma unroll 1
-  for (int q = warp; q * S::MQ < a.mxp; q += S::WARPS) {
-    T acc2[S::MQ][MYP];
-#pragma unroll
-    for (int k = 0; k < S::MQ; ++k)
-#pragma unroll
-      for (int n = 0; n < MYP; ++n) acc2[k][n] = T(0);
-#pragma unroll 2
-    for (int xl = 0; xl < S::XB; ++xl) {
-      T s[S::MQ];
-#pragma unroll
-      for (int k = 0; k < S::MQ; ++k) s[k] = sxs[xl * a.mxp + q * S::MQ + k];
-#pragma unroll
-      for (int n = 0; n < MYP; ++n) {
-        const T av = abuf[(xl * MYP + n) * S::ZC + lane];
-#pragma unroll
-        for (int k = 0; k < S::MQ; ++k) acc2[k][n] = fma(s[k], av, acc2[k][n]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < S::MQ; ++k)
-#pragma unroll
-      for (int n = 0; n < MYP; ++n) red[((q * S::MQ + k) * MYP + n) * S::ZC + lane] = acc2[k][n];
-  }
-
-  // the cluster's blocks summed: CTA `rank` takes mode columns
-  // [rank * per, (rank + 1) * per) and reads them from every CTA in rank order
+  // x modes, in rounds of mode_round_modes: warp w takes the passes of MQ
+  // modes q = w, w + WARPS, ... of the round; then the cluster's blocks are
+  // summed for the round's columns: CTA `rank` takes a slice of them and
+  // reads them from every CTA in rank order
   mcg::cluster_group cl = mcg::this_cluster();
-  cl.sync();                       // every block's projection is complete
   const int ncl = int(cl.num_blocks()), rank = int(cl.block_rank());
-  const int per = (a.mc + ncl - 1) / ncl;
-  const int c0 = rank * per, c1 = c0 + per < a.mc ? c0 + per : a.mc;
   T* out = a.part + size_t(blockIdx.y / ncl) * a.mc * a.nz + z0 + lane;
+  const int mpr = mode_round_modes<T>(a.mxp);
 #pragma unroll 1
-  for (int c = c0 + warp; c < c1; c += S::WARPS) {
-    T sum = T(0);
+  for (int m0 = 0; m0 < a.mxp; m0 += mpr) {
+    const int m1 = m0 + mpr < a.mxp ? m0 + mpr : a.mxp;
 #pragma unroll 1
-    for (int r = 0; r < ncl; ++r) sum += cl.map_shared_rank(red, r)[c * S::ZC + lane];
-    out[size_t(c) * a.nz] = sum;
+    for (int q = m0 / S::MQ + warp; q * S::MQ < m1; q += S::WARPS) {
+      T acc2[S::MQ][MYP];
+#pragma unroll
+      for (int k = 0; k < S::MQ; ++k)
+#pragma unroll
+        for (int n = 0; n < MYP; ++n) acc2[k][n] = T(0);
+#pragma unroll 2
+      for (int xl = 0; xl < S::XB; ++xl) {
+        T s[S::MQ];
+#pragma unroll
+        for (int k = 0; k < S::MQ; ++k) s[k] = sxs[xl * a.mxp + q * S::MQ + k];
+#pragma unroll
+        for (int n = 0; n < MYP; ++n) {
+          const T av = abuf[(xl * MYP + n) * S::ZC + lane];
+#pragma unroll
+          for (int k = 0; k < S::MQ; ++k) acc2[k][n] = fma(s[k], av, acc2[k][n]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < S::MQ; ++k)
+#pragma unroll
+        for (int n = 0; n < MYP; ++n) red[((q * S::MQ + k - m0) * MYP + n) * S::ZC + lane] = acc2[k][n];
+    }
+    cl.sync();                     // every block's projection of the round is complete
+    const int nc = (m1 - m0) * MYP;
+    const int per = (nc + ncl - 1) / ncl;
+    const int c0 = rank * per, c1 = c0 + per < nc ? c0 + per : nc;
+#pragma unroll 1
+    for (int c = c0 + warp; c < c1; c += S::WARPS) {
+      T sum = T(0);
+#pragma unroll 1
+      for (int r = 0; r < ncl; ++r) sum += cl.map_shared_rank(red, r)[c * S::ZC + lane];
+      out[size_t(m0 * MYP + c) * a.nz] = sum;
+    }
+    cl.sync();                     // no CTA overwrites (or leaves) while its projection is still read
   }
-  cl.sync();                       // no CTA leaves while its projection is still read
 }
 
 // Back-projection of one (z chunk, x block): each thread forms, for its XPW x
