@@ -360,7 +360,8 @@ def bench_batched(args, count=96):
     import torch
 
     from inputs import bunches
-    from paper_1111_4971_gb300 import PipeSolver, batch_plan_info, batch_side_streams, batch_status, solve_batched
+    from paper_1111_4971_gb300 import (PipeSolver, batch_grouped, batch_plan_info, batch_side_streams, batch_status,
+                                       solve_batched)
     items = bunches.workload_batched_96(count=count)
     solvers, rhos = [], []
     for it in items:
@@ -396,13 +397,16 @@ def bench_batched(args, count=96):
         batch_ms = timed(g.replay)
     ok = batch_status(solvers) == 0
     persistent, order = batch_plan_info(solvers)
+    grouped, ngroups = batch_grouped(solvers, with_groups=True)
     return {"solves": count, "grids": grids, "batched_ms": batch_ms, "loop_ms": loop_ms,
             "batched_solves_per_s": count / (batch_ms * 1e-3),
             "loop_solves_per_s": count / (loop_ms * 1e-3), "speedup": loop_ms / batch_ms,
             "status_ok": ok, "persistent_solves": persistent,
             "order": ["stage-major", "pipelined", "L2-local"][order],
-            "launches_per_batch": (1 if persistent else 0) + 3 * (count - persistent),
-            "side_streams": batch_side_streams(solvers)}
+            "launches_per_batch": (1 if persistent else 0) + 3 * (count - persistent - grouped) + 3 * ngroups,
+            "side_streams": batch_side_streams(solvers),
+            # mode-form solves of one shape run as one launch per stage
+            "grouped_solves": grouped, "groups": ngroups}
 
 
 def bench_banded(args):

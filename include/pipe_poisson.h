@@ -266,6 +266,20 @@ int pipe_batch_side_streams(pipe_handle* const* handles, int n, int* nside);
  * pointers, or no tuned plan for this set). */
 int pipe_batch_select_streams(pipe_handle* const* handles, int n, int nside);
 
+/* Mode-form groups of the batched call: FP32 solves outside the persistent
+ * launch that run the mode-space form with the occupancy-laid-out kernels
+ * (pipe_get_plan t_kind 3 on a mesh symmetric in y, ny/2 in {16, 32, 64})
+ * and share nx, ny, nz, the mode counts and the y-mode table run together:
+ * one launch per stage for up to 64 solves, with the same kernels and the
+ * same results, bit for bit, as their single-solve launches.  The tuner
+ * times the call with and without them.  pipe_batch_grouped reports how
+ * many solves the tuned plan runs that way (0: none) and, if `groups` is not
+ * null, in how many groups; pipe_batch_select_groups
+ * sets it on (1) or off (0) for later calls, for tests and experiments.
+ * Errors: PIPE_EINVAL as pipe_batch_side_streams. */
+int pipe_batch_grouped(pipe_handle* const* handles, int n, int* grouped, int* groups);
+int pipe_batch_select_groups(pipe_handle* const* handles, int n, int on);
+
 /* Override that choice for later calls with this exact handle set: `variant`
  * k runs persistent the solves whose z spectrum is smaller than the k-th
  * largest distinct spectrum size of the set (k = 0: every solve), `order` as

@@ -20,7 +20,7 @@ from ._lib import PipeError, PipeGeometry, PipeGrid, check
 
 __all__ = ["PipeSolver", "PipePoissonFunction", "CICDeposit", "solve_batched", "batch_status",
            "batch_inject_fault", "batch_plan_info", "batch_select", "batch_side_streams",
-           "batch_select_streams", "PipeError", "field_energy"]
+           "batch_select_streams", "batch_grouped", "batch_select_groups", "PipeError", "field_energy"]
 
 
 def _stream_ptr(stream):
@@ -302,6 +302,25 @@ def batch_side_streams(solvers):
     k = ctypes.c_int(0)
     check(lib.pipe_batch_side_streams(hs, n, ctypes.byref(k)), "pipe_batch_side_streams")
     return k.value
+
+
+def batch_grouped(solvers, with_groups=False):
+    """Solves the tuned batched call runs in mode-form groups (pipe_batch_grouped);
+    with_groups: (solves, groups)."""
+    lib = _lib.load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    k, g = ctypes.c_int(-1), ctypes.c_int(-1)
+    check(lib.pipe_batch_grouped(hs, n, ctypes.byref(k), ctypes.byref(g)), "pipe_batch_grouped")
+    return (k.value, g.value) if with_groups else k.value
+
+
+def batch_select_groups(solvers, on):
+    """Run the mode-form groups together (True) or solve by solve (pipe_batch_select_groups)."""
+    lib = _lib.load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    check(lib.pipe_batch_select_groups(hs, n, 1 if on else 0), "pipe_batch_select_groups")
 
 
 def batch_select_streams(solvers, nside):

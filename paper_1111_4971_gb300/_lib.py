@@ -54,6 +54,8 @@ SIGNATURES = {
     "pipe_batch_plan_info": (c_int, [POINTER(H), c_int, POINTER(c_int), POINTER(c_int)]),
     "pipe_batch_side_streams": (c_int, [POINTER(H), c_int, POINTER(c_int)]),
     "pipe_batch_select_streams": (c_int, [POINTER(H), c_int, c_int]),
+    "pipe_batch_grouped": (c_int, [POINTER(H), c_int, POINTER(c_int), POINTER(c_int)]),
+    "pipe_batch_select_groups": (c_int, [POINTER(H), c_int, c_int]),
     "pipe_batch_select": (c_int, [POINTER(H), c_int, c_int, c_int]),
     "pipe_green_spectrum": (c_int, [H, POINTER(c_double), c_size_t]),
     "pipe_stage_z_forward": (c_int, [H, c_void_p, c_void_p, c_int, c_void_p]),

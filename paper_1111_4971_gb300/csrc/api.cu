@@ -285,6 +285,11 @@ int mode_stage(const pipe_handle* h, int stage, const void* rho, void* phi, void
   return status_of(launch_mode_stage<T>(stage, h->myp, h->fy != 0, a, st));
 }
 
+ModeArgs<float> mode_args_f32(const pipe_handle* h) {
+  void* psi = static_cast<char*>(h->mwork) + sizeof(float) * size_t(mode_xblocks(h)) * h->mxp * h->myp * h->grid.nz;
+  return mode_args<float>(h, nullptr, nullptr, h->mwork, psi);
+}
+
 int mode_solve(pipe_handle* h, const void* rho, void* phi, void* scratch, cudaStream_t st) {
   const size_t esz = h->grid.dtype == PIPE_F64 ? 8 : 4;
   void* psi = static_cast<char*>(scratch) + esz * size_t(mode_xblocks(h)) * h->mxp * h->myp * h->grid.nz;

@@ -27,6 +27,8 @@
 
 #include "../../include/pipe_poisson.h"
 #include "handle.cuh"
+#include "modes.cuh"
+#include "modes_impl.cuh"
 #include "tdst_impl.cuh"
 #include "tsym_impl.cuh"
 #include "zfft_impl.cuh"
@@ -233,6 +235,18 @@ int z_cols(int nz) {
   return 0;
 }
 
+// FP32 mode-form solves outside the persistent launch that share a shape and
+// a y-mode table: one launch per stage for all of them (ModeGroup), the same
+// kernels and arithmetic per solve as their single-solve launches
+struct MGroup {
+  std::vector<int> members;            // indices into the handle set
+  ModeArgs<float>* dargs = nullptr;    // [members] in device memory: tables and scratch
+  ModeArgs<float> a0{};                // the shape (members[0]'s arguments)
+  int myp = 0;
+  int zgroups = 0;                     // partial projections the z stage sums
+  const float* sy = nullptr;           // the shared y-mode table (host copy)
+};
+
 // One way of running a handle set: the solves in the persistent launch
 // ("members", with their work lists) and the solves left to their own
 // single-solve launches ("outside").
@@ -250,6 +264,7 @@ struct BatchVariant {
   size_t smem = 0;
   int grid = 0;
   int order = 0;
+  std::vector<MGroup> mgroups;   // groups among `outside` (two or more solves each)
 };
 
 // Built and timed on the first call for a handle set, kept by handles[0].
@@ -276,6 +291,7 @@ struct BatchPlan {
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kSide] = {};
   int nside = 0;
+  int group = 0;                // the mode-form groups launched together (1) or solve by solve (0)
 };
 
 // the side streams and their events, created on first use
@@ -290,6 +306,7 @@ int side_streams(BatchPlan* b) {
 }
 
 void variant_release(BatchVariant& v) {
+  for (MGroup& g : v.mgroups) cudaFree(g.dargs);
   cudaFree(v.solves);
   for (int k = 0; k < 3; ++k) cudaFree(v.lists[k]);
   cudaFree(v.need);
@@ -487,6 +504,68 @@ static double spectrum_bytes(const pipe_handle* h) {
   return double(h->grid.nx) * h->grid.ny * (h->grid.nz + 1) * (h->grid.dtype == PIPE_F64 ? 16 : 8);
 }
 
+// the groups of a variant's outside solves: FP32 mode-form solves with the
+// occupancy-laid-out kernels, of one shape and one y-mode table, up to
+// kMaxModeGroup each; only groups of two or more are kept
+static bool mode_groupable(const pipe_handle* h) {
+  return h->grid.dtype == PIPE_F32 && h->use_modes && h->mfast && h->banded < 0 && h->msy_host;
+}
+static bool same_mode_shape(const pipe_handle* a, const pipe_handle* b) {
+  if (a->grid.nx != b->grid.nx || a->grid.ny != b->grid.ny || a->grid.nz != b->grid.nz ||
+      a->geom.modes_m != b->geom.modes_m || a->mxp != b->mxp || a->myp != b->myp || a->fy != b->fy)
+    return false;
+  const size_t nsy = size_t(a->grid.ny / 2) * a->myp;
+  return std::memcmp(a->msy_host, b->msy_host, nsy * sizeof(float)) == 0;
+}
+static int build_mode_groups(pipe_handle* const* hs, BatchVariant* v) {
+  std::vector<MGroup> gs;
+  for (int s : v->outside) {
+    if (!mode_groupable(hs[s])) continue;
+    MGroup* into = nullptr;
+    for (MGroup& g : gs)
+      if (int(g.members.size()) < kMaxModeGroup && same_mode_shape(hs[g.members[0]], hs[s])) { into = &g; break; }
+    if (!into) {
+      gs.emplace_back();
+      into = &gs.back();
+    }
+    into->members.push_back(s);
+  }
+  for (MGroup& g : gs) {
+    if (g.members.size() < 2) continue;
+    const pipe_handle* h0 = hs[g.members[0]];
+    std::vector<ModeArgs<float>> args;
+    for (int s : g.members) args.push_back(mode_args_f32(hs[s]));
+    g.a0 = args[0];
+    g.myp = h0->myp;
+    g.zgroups = mode_xblocks(h0);
+    g.sy = h0->msy_host;
+    if (cudaMalloc(&g.dargs, sizeof(ModeArgs<float>) * args.size()) != cudaSuccess) return PIPE_ENOMEM;
+    if (cudaMemcpy(g.dargs, args.data(), sizeof(ModeArgs<float>) * args.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      cudaFree(g.dargs);
+      return PIPE_ECUDA;
+    }
+    v->mgroups.push_back(g);
+  }
+  return PIPE_OK;
+}
+
+// the three stages of one mode group on stream st
+static int run_mode_group(const MGroup& g, const void* const* rho, void* const* phi, cudaStream_t st) {
+  ModeGroup p{};
+  p.args = g.dargs;
+  p.n = int(g.members.size());
+  p.nz = g.a0.nz;
+  for (int i = 0; i < p.n; ++i) {
+    p.rho[i] = static_cast<const float*>(rho[g.members[i]]);
+    p.phi[i] = static_cast<float*>(phi[g.members[i]]);
+  }
+  cudaError_t e = launch_mode_fast_group(0, g.myp, g.a0, p, g.sy, st);
+  if (e == cudaSuccess) e = launch_mode_z_warp_group(g.a0, g.zgroups, p, st);
+  if (e == cudaSuccess) e = launch_mode_fast_group(2, g.myp, g.a0, p, g.sy, st);
+  return e == cudaSuccess ? PIPE_OK : PIPE_ECUDA;
+}
+
 template <typename T>
 static int build_plan(pipe_handle* const* hs, int n, BatchPlan* b) {
   std::vector<double> sizes;
@@ -504,6 +583,10 @@ static int build_plan(pipe_handle* const* hs, int n, BatchPlan* b) {
       const int st = build_variant<T>(hs, &v);
       if (st != PIPE_OK) return st;
     }
+    if (sizeof(T) == 4) {
+      const int st = build_mode_groups(hs, &v);
+      if (st != PIPE_OK) return st;
+    }
     b->nvar = k + 1;
   }
   return PIPE_OK;
@@ -511,17 +594,24 @@ static int build_plan(pipe_handle* const* hs, int n, BatchPlan* b) {
 
 // one batched call with variant v: the persistent launch, then the solves
 // outside it, in order on stream st (nside = 0) or dealt round-robin to the
-// side streams, which start after the persistent launch and rejoin st
-static int run_variant(BatchPlan* b, int v, int nside, pipe_handle* const* hs, const void* const* rho,
+// side streams, which start after the persistent launch and rejoin st; with
+// grp, each mode group's three launches take one slot of that order
+static int run_variant(BatchPlan* b, int v, int nside, int grp, pipe_handle* const* hs, const void* const* rho,
                        void* const* phi, cudaStream_t st) {
   BatchVariant& x = b->var[v];
   int r = b->dtype == PIPE_F64 ? launch_variant<double>(&x, rho, phi, b->drop_stage, b->spin_limit, st)
                                : launch_variant<float>(&x, rho, phi, b->drop_stage, b->spin_limit, st);
   if (r != PIPE_OK || x.outside.empty()) return r;
+  std::vector<char> grouped(b->n, 0);
+  if (grp)
+    for (const MGroup& g : x.mgroups)
+      for (int s : g.members) grouped[s] = 1;
   if (nside == 0) {
+    if (grp)
+      for (size_t k = 0; r == PIPE_OK && k < x.mgroups.size(); ++k) r = run_mode_group(x.mgroups[k], rho, phi, st);
     for (size_t k = 0; r == PIPE_OK && k < x.outside.size(); ++k) {
       const int s = x.outside[k];
-      r = handle_solve(hs[s], rho[s], phi[s], false, st);
+      if (!grouped[s]) r = handle_solve(hs[s], rho[s], phi[s], false, st);
     }
     return r;
   }
@@ -529,9 +619,13 @@ static int run_variant(BatchPlan* b, int v, int nside, pipe_handle* const* hs, c
   if (cudaEventRecord(b->fork, st) != cudaSuccess) return PIPE_ECUDA;
   for (int i = 0; i < nside; ++i)
     if (cudaStreamWaitEvent(b->side[i], b->fork, 0) != cudaSuccess) return PIPE_ECUDA;
+  size_t slot = 0;
+  if (grp)
+    for (size_t k = 0; r == PIPE_OK && k < x.mgroups.size(); ++k)
+      r = run_mode_group(x.mgroups[k], rho, phi, b->side[slot++ % nside]);
   for (size_t k = 0; r == PIPE_OK && k < x.outside.size(); ++k) {
     const int s = x.outside[k];
-    r = handle_solve(hs[s], rho[s], phi[s], false, b->side[k % nside]);
+    if (!grouped[s]) r = handle_solve(hs[s], rho[s], phi[s], false, b->side[slot++ % nside]);
   }
   // rejoin even after an error, so that a capture is never left unjoined
   for (int i = 0; i < nside; ++i) {
@@ -587,25 +681,26 @@ extern "C" int pipe_poisson_solve_batched(pipe_handle* const* handles, const voi
       // time every (variant, work-list order) once after a warm-up run and
       // keep the fastest; these runs are valid solves
       float best = 1e30f;
-      int pick_v = 0, pick_o = 0, pick_s = 0;
+      int pick_v = 0, pick_o = 0, pick_s = 0, pick_g = 0;
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       for (int v = 0; v < b->nvar && st == PIPE_OK; ++v)
         for (int k = 0; k < (b->var[v].n > 0 ? 3 : 1) && st == PIPE_OK; ++k)
-          for (int ns : {0, 2, 3}) {
-            if (ns > 0 && b->var[v].outside.size() < size_t(ns)) continue;
-            if (st != PIPE_OK) break;
-            b->var[v].items = b->var[v].lists[k];
-            st = run_variant(b, v, ns, handles, rho, phi, s);
-            cudaEventRecord(e0, s);
-            if (st == PIPE_OK) st = run_variant(b, v, ns, handles, rho, phi, s);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (st == PIPE_OK && ms < best) { best = ms; pick_v = v; pick_o = k; pick_s = ns; }
-          }
+          for (int ns : {0, 2, 3})
+            for (int grp = 0; grp < (b->var[v].mgroups.empty() ? 1 : 2); ++grp) {
+              if (ns > 0 && b->var[v].outside.size() < size_t(ns)) continue;
+              if (st != PIPE_OK) break;
+              b->var[v].items = b->var[v].lists[k];
+              st = run_variant(b, v, ns, grp, handles, rho, phi, s);
+              cudaEventRecord(e0, s);
+              if (st == PIPE_OK) st = run_variant(b, v, ns, grp, handles, rho, phi, s);
+              cudaEventRecord(e1, s);
+              cudaEventSynchronize(e1);
+              float ms = 0.f;
+              cudaEventElapsedTime(&ms, e0, e1);
+              if (st == PIPE_OK && ms < best) { best = ms; pick_v = v; pick_o = k; pick_s = ns; pick_g = grp; }
+            }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       for (int v = 0; v < b->nvar; ++v) {
@@ -614,11 +709,12 @@ extern "C" int pipe_poisson_solve_batched(pipe_handle* const* handles, const voi
       }
       b->chosen = pick_v;
       b->nside = pick_s;
+      b->group = pick_g;
       b->tuned = true;
     }
     // an injected fault is meant for the persistent launch: run every solve there
     const int v = b->drop_stage >= 0 ? 0 : b->chosen;
-    if (st == PIPE_OK) st = run_variant(b, v, b->nside, handles, rho, phi, s);
+    if (st == PIPE_OK) st = run_variant(b, v, b->nside, b->group, handles, rho, phi, s);
     b->last = v;
     b->drop_stage = -1;
     b->spin_limit = 1ll << 22;
@@ -680,6 +776,33 @@ extern "C" int pipe_batch_select_streams(pipe_handle* const* handles, int n, int
   for (int s = 0; s < n; ++s)
     if (b->handles[s] != handles[s]) return PIPE_EINVAL;
   b->nside = nside;
+  return PIPE_OK;
+}
+
+extern "C" int pipe_batch_grouped(pipe_handle* const* handles, int n, int* grouped, int* groups) {
+  if (!handles || n < 1 || !handles[0] || !grouped) return PIPE_EINVAL;
+  BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
+  if (!b || b->n != n || !b->tuned) return PIPE_EINVAL;
+  for (int s = 0; s < n; ++s)
+    if (b->handles[s] != handles[s]) return PIPE_EINVAL;
+  int k = 0, ng = 0;
+  if (b->group)
+    for (const MGroup& g : b->var[b->chosen].mgroups) {
+      k += int(g.members.size());
+      ++ng;
+    }
+  *grouped = k;
+  if (groups) *groups = ng;
+  return PIPE_OK;
+}
+
+extern "C" int pipe_batch_select_groups(pipe_handle* const* handles, int n, int on) {
+  if (!handles || n < 1 || !handles[0] || (on != 0 && on != 1)) return PIPE_EINVAL;
+  BatchPlan* b = static_cast<BatchPlan*>(handles[0]->batch);
+  if (!b || b->n != n || !b->tuned) return PIPE_EINVAL;
+  for (int s = 0; s < n; ++s)
+    if (b->handles[s] != handles[s]) return PIPE_EINVAL;
+  b->group = on;
   return PIPE_OK;
 }
 

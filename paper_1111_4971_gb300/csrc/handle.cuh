@@ -91,4 +91,8 @@ int mode_solve(pipe_handle* h, const void* rho, void* phi, void* scratch, cudaSt
 size_t mode_scratch_bytes(const pipe_handle* h);
 // x blocks of the projection (nx / rows per CTA of the dtype)
 int mode_xblocks(const pipe_handle* h);
+// the FP32 mode-form arguments of a handle with its own scratch as part /
+// psi (rho, phi null): the batched call's grouped launches
+template <typename T> struct ModeArgs;
+ModeArgs<float> mode_args_f32(const pipe_handle* h);
 }  // namespace pp

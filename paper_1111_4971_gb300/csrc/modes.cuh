@@ -86,14 +86,31 @@ inline int mode_cluster(int xblocks) {
 template <typename T>
 cudaError_t launch_mode_stage(int stage, int myp, bool fy, const ModeArgs<T>& a, cudaStream_t st);
 
+// A group of FP32 mode-form solves of one shape (nx, ny, nz, mode layout)
+// and one y-mode table, run by one launch per stage (the batched call):
+// args[s] (device memory) holds solve s's tables and scratch, rho / phi its
+// field arrays (kernel parameters, so that a captured launch keeps them).
+constexpr int kMaxModeGroup = 64;
+struct ModeGroup {
+  const ModeArgs<float>* args;
+  const float* rho[kMaxModeGroup];
+  float* phi[kMaxModeGroup];
+  int n;
+  int nz;
+};
+
 // the FP32 z convolution, one warp-level FFT per mode column (modes_z.cu):
 // nz in 32..1024, groups partial projections summed on load
 cudaError_t launch_mode_z_warp(const ModeArgs<float>& a, int groups, cudaStream_t st);
+// the same for a group (columns of solve s in the CTAs s * cps ..)
+cudaError_t launch_mode_z_warp_group(const ModeArgs<float>& a, int groups, const ModeGroup& g, cudaStream_t st);
 
 // the FP32 projection and back-projection laid out for occupancy
 // (modes_fast.cu): meshes symmetric in y with ny/2 in {16, 32, 64}
 bool mode_fast_ok(int ny, int nx, int myp, bool fy);
 // sy_host: the FP32 y-mode table [ny/2][myp] in host memory (the projection's parameter)
 cudaError_t launch_mode_fast(int stage, int myp, const ModeArgs<float>& a, const float* sy_host, cudaStream_t st);
+cudaError_t launch_mode_fast_group(int stage, int myp, const ModeArgs<float>& a, const ModeGroup& g,
+                                   const float* sy_host, cudaStream_t st);
 
 }  // namespace pp

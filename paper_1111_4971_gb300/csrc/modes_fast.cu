@@ -109,10 +109,10 @@ constexpr int kCS = kZC + 1;
 template <int MYP>
 constexpr int back_rows_per_thread() { return MYP <= 20 ? 2 : 1; }
 
-// one thread per (x row, z): the 16 warps of a CTA take its 16 x rows
+// one thread per (x row, z): the 16 warps of a CTA take its 16 x rows; the
+// CTA's tile is z chunk zc, x block xb (its cluster: consecutive x blocks)
 template <int NYH, int MYP>
-__global__ void __launch_bounds__(32 * kW, 2)
-    mode_project_fast_kernel(ModeArgs<float> a, const __grid_constant__ SyTab<NYH, MYP> tab) {
+__device__ __forceinline__ void project_fast(const ModeArgs<float>& a, const SyTab<NYH, MYP>& tab, int zc, int xb) {
   constexpr int RS = slot_a<MYP>();
   constexpr int KS = kX / 8;                                   // k steps over the CTA's x rows
   constexpr int NS = NYH / kPairs;                             // ring stages over the half rows
@@ -121,8 +121,8 @@ __global__ void __launch_bounds__(32 * kW, 2)
   float* red = abuf + kX * RS;                                 // [mc][33]: P[m][n][z]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int z0 = int(blockIdx.x) * kZC;
-  const int xb0 = int(blockIdx.y) * kX;
+  const int z0 = zc * kZC;
+  const int xb0 = xb * kX;
   const int ny = 2 * NYH;
 
   float* ring = abuf + warp * RS;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(32 * kW, 2)
   const int ncl = int(cl.num_blocks()), rank = int(cl.block_rank());
   const int per = (a.mc + ncl - 1) / ncl;
   const int c0 = rank * per, c1 = c0 + per < a.mc ? c0 + per : a.mc;
-  float* out = a.part + size_t(blockIdx.y / ncl) * a.mc * a.nz + z0 + lane;
+  float* out = a.part + size_t(xb / ncl) * a.mc * a.nz + z0 + lane;
 #pragma unroll 1
   for (int c = c0 + warp; c < c1; c += kW) {
     float v[8];
@@ -254,8 +254,7 @@ __device__ __forceinline__ void back_rows(const float (&bv)[XR][MYP], const SyTa
 }
 
 template <int NYH, int MYP>
-__global__ void __launch_bounds__(32 * kW, 2)
-    mode_back_fast_kernel(ModeArgs<float> a, const __grid_constant__ SyTab<NYH, MYP> tab) {
+__device__ __forceinline__ void back_fast(const ModeArgs<float>& a, const SyTab<NYH, MYP>& tab, int zc, int xb) {
   constexpr int RS = rows_p<MYP>(), BS = rows_b<MYP>();
   constexpr int XT = kX / 8;                         // n tiles over the CTA's x rows
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -264,8 +263,8 @@ __global__ void __launch_bounds__(32 * kW, 2)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int pair = warp % (kW / 2), half = warp / (kW / 2);
-  const int z0 = int(blockIdx.x) * kZC;
-  const int xb0 = int(blockIdx.y) * kX;
+  const int z0 = zc * kZC;
+  const int xb0 = xb * kX;
   const int ny = 2 * NYH;
   for (int idx = threadIdx.x; idx < a.mx * MYP * (kZC / 4); idx += 32 * kW) {
     const int c = idx / (kZC / 4), piece = idx % (kZC / 4);
@@ -331,6 +330,38 @@ __global__ void __launch_bounds__(32 * kW, 2)
     back_rows<NYH, MYP, XR, NYH / 2, NYH / 2>(bv, tab, base, a.nz, ny * a.nz);
 }
 
+// one solve: grid (nz / 32, nx / 16)
+template <int NYH, int MYP>
+__global__ void __launch_bounds__(32 * kW, 2)
+    mode_project_fast_kernel(ModeArgs<float> a, const __grid_constant__ SyTab<NYH, MYP> tab) {
+  project_fast<NYH, MYP>(a, tab, int(blockIdx.x), int(blockIdx.y));
+}
+template <int NYH, int MYP>
+__global__ void __launch_bounds__(32 * kW, 2)
+    mode_back_fast_kernel(ModeArgs<float> a, const __grid_constant__ SyTab<NYH, MYP> tab) {
+  back_fast<NYH, MYP>(a, tab, int(blockIdx.x), int(blockIdx.y));
+}
+
+// a group of solves of one shape and one y-mode table (ModeGroup): grid
+// (n * nz / 32, nx / 16), solve s taking the z chunks s * nz/32 ..; the
+// same arithmetic per solve as the single-solve kernels
+template <int NYH, int MYP>
+__global__ void __launch_bounds__(32 * kW, 2)
+    mode_project_group_kernel(const __grid_constant__ ModeGroup g, const __grid_constant__ SyTab<NYH, MYP> tab) {
+  const int zpc = g.nz / kZC, s = int(blockIdx.x) / zpc;
+  ModeArgs<float> a = g.args[s];
+  a.rho = g.rho[s];
+  project_fast<NYH, MYP>(a, tab, int(blockIdx.x) % zpc, int(blockIdx.y));
+}
+template <int NYH, int MYP>
+__global__ void __launch_bounds__(32 * kW, 2)
+    mode_back_group_kernel(const __grid_constant__ ModeGroup g, const __grid_constant__ SyTab<NYH, MYP> tab) {
+  const int zpc = g.nz / kZC, s = int(blockIdx.x) / zpc;
+  ModeArgs<float> a = g.args[s];
+  a.phi = g.phi[s];
+  back_fast<NYH, MYP>(a, tab, int(blockIdx.x) % zpc, int(blockIdx.y));
+}
+
 namespace {
 
 template <typename K>
@@ -339,17 +370,21 @@ cudaError_t big_smem(K kern, size_t smem) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
 }
 
+// stage `which` (0 projection, 1 back-projection) of one solve (g == nullptr)
+// or of a group of solves shaped like `a`
 template <int NYH, int MYP>
-cudaError_t launch_fast(int which, const ModeArgs<float>& a, const float* sy_host, cudaStream_t st) {
+cudaError_t launch_fast(int which, const ModeArgs<float>& a, const ModeGroup* g, const float* sy_host,
+                        cudaStream_t st) {
   const int xblocks = a.nx / kX;
-  const dim3 grid(unsigned(a.nz / kZC), unsigned(xblocks));
+  const dim3 grid(unsigned((g ? g->n : 1) * (a.nz / kZC)), unsigned(xblocks));
   SyTab<NYH, MYP> tab;
   for (int i = 0; i < NYH * MYP; ++i) tab.s[i] = sy_host[i];
   cudaError_t e;
   if (which == 0) {
     const size_t smem = sizeof(float) * (size_t(kX) * slot_a<MYP>() + size_t(a.mc) * kCS);
     void (*kern)(ModeArgs<float>, const SyTab<NYH, MYP>) = mode_project_fast_kernel<NYH, MYP>;
-    if ((e = big_smem(kern, smem)) != cudaSuccess) return e;
+    void (*gkern)(const ModeGroup, const SyTab<NYH, MYP>) = mode_project_group_kernel<NYH, MYP>;
+    if ((e = g ? big_smem(gkern, smem) : big_smem(kern, smem)) != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = dim3(32 * kW, 1, 1);
@@ -362,24 +397,38 @@ cudaError_t launch_fast(int which, const ModeArgs<float>& a, const float* sy_hos
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a, tab);
+    return g ? cudaLaunchKernelEx(&cfg, gkern, *g, tab) : cudaLaunchKernelEx(&cfg, kern, a, tab);
   }
   const size_t smem = sizeof(float) * (size_t(a.mx) * rows_p<MYP>() + size_t(kX) * rows_b<MYP>());
   void (*kern)(ModeArgs<float>, const SyTab<NYH, MYP>) = mode_back_fast_kernel<NYH, MYP>;
-  if ((e = big_smem(kern, smem)) != cudaSuccess) return e;
-  kern<<<grid, 32 * kW, smem, st>>>(a, tab);
+  void (*gkern)(const ModeGroup, const SyTab<NYH, MYP>) = mode_back_group_kernel<NYH, MYP>;
+  if ((e = g ? big_smem(gkern, smem) : big_smem(kern, smem)) != cudaSuccess) return e;
+  if (g) gkern<<<grid, 32 * kW, smem, st>>>(*g, tab);
+  else kern<<<grid, 32 * kW, smem, st>>>(a, tab);
   return cudaGetLastError();
 }
 
 template <int NYH>
-cudaError_t launch_fast2(int which, int myp, const ModeArgs<float>& a, const float* sy_host, cudaStream_t st) {
+cudaError_t launch_fast2(int which, int myp, const ModeArgs<float>& a, const ModeGroup* g, const float* sy_host,
+                         cudaStream_t st) {
   switch (myp) {
-    case 8: return launch_fast<NYH, 8>(which, a, sy_host, st);
-    case 12: return launch_fast<NYH, 12>(which, a, sy_host, st);
-    case 16: return launch_fast<NYH, 16>(which, a, sy_host, st);
-    case 20: return launch_fast<NYH, 20>(which, a, sy_host, st);
-    case 24: return launch_fast<NYH, 24>(which, a, sy_host, st);
-    case 32: return launch_fast<NYH, 32>(which, a, sy_host, st);
+    case 8: return launch_fast<NYH, 8>(which, a, g, sy_host, st);
+    case 12: return launch_fast<NYH, 12>(which, a, g, sy_host, st);
+    case 16: return launch_fast<NYH, 16>(which, a, g, sy_host, st);
+    case 20: return launch_fast<NYH, 20>(which, a, g, sy_host, st);
+    case 24: return launch_fast<NYH, 24>(which, a, g, sy_host, st);
+    case 32: return launch_fast<NYH, 32>(which, a, g, sy_host, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fast_any(int stage, int myp, const ModeArgs<float>& a, const ModeGroup* g, const float* sy_host,
+                            cudaStream_t st) {
+  const int which = stage == 0 ? 0 : 1;
+  switch (a.ny / 2) {
+    case 16: return launch_fast2<16>(which, myp, a, g, sy_host, st);
+    case 32: return launch_fast2<32>(which, myp, a, g, sy_host, st);
+    case 64: return launch_fast2<64>(which, myp, a, g, sy_host, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -395,13 +444,15 @@ bool mode_fast_ok(int ny, int nx, int myp, bool fy) {
 // stage 0 (projection) or 2 (back-projection) of an FP32 handle that
 // mode_fast_ok accepts
 cudaError_t launch_mode_fast(int stage, int myp, const ModeArgs<float>& a, const float* sy_host, cudaStream_t st) {
-  const int which = stage == 0 ? 0 : 1;
-  switch (a.ny / 2) {
-    case 16: return launch_fast2<16>(which, myp, a, sy_host, st);
-    case 32: return launch_fast2<32>(which, myp, a, sy_host, st);
-    case 64: return launch_fast2<64>(which, myp, a, sy_host, st);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_fast_any(stage, myp, a, nullptr, sy_host, st);
+}
+
+// the same stage for a group of such solves of one shape and one y-mode table
+// (g->args[s] shaped like a)
+cudaError_t launch_mode_fast_group(int stage, int myp, const ModeArgs<float>& a, const ModeGroup& g,
+                                   const float* sy_host, cudaStream_t st) {
+  if (g.n < 1 || g.n > kMaxModeGroup) return cudaErrorInvalidValue;
+  return launch_fast_any(stage, myp, a, &g, sy_host, st);
 }
 
 }  // namespace pp

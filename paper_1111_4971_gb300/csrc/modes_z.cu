@@ -49,8 +49,9 @@ struct ZWarpShape {
   static constexpr size_t SMEM = sizeof(float2) * (2 * size_t(L) + size_t(kZWarps) * CPW * 2 * CB) + sizeof(float) * GS;
 };
 
+// CTA `blk` of a solve: its columns blk * CPC ..
 template <int L>
-__global__ void __launch_bounds__(32 * kZWarps) mode_z_warp_kernel(ModeArgs<float> a, int groups) {
+__device__ __forceinline__ void z_warp(const ModeArgs<float>& a, int groups, int blk) {
   using V = float2;
   using Sh = ZWarpShape<L>;
   constexpr int S = Sh::S, E = Sh::E, CPW = Sh::CPW;
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(32 * kZWarps) mode_z_warp_kernel(ModeArgs<floa
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sub = lane / S, b = lane % S;
   const int cl = warp * CPW + sub;               // column within the CTA
-  const int col0 = int(blockIdx.x) * CPC;
+  const int col0 = blk * CPC;
   const int col = col0 + cl;
   const bool valid = col < a.mc;
   // shared memory: the stage-2 twiddles tw[k1][b] = w_L^{b k1}, the spectral
@@ -175,30 +176,57 @@ __global__ void __launch_bounds__(32 * kZWarps) mode_z_warp_kernel(ModeArgs<floa
 }
 
 template <int L>
-cudaError_t launch_zw(const ModeArgs<float>& a, int groups, cudaStream_t st) {
+__global__ void __launch_bounds__(32 * kZWarps) mode_z_warp_kernel(ModeArgs<float> a, int groups) {
+  z_warp<L>(a, groups, int(blockIdx.x));
+}
+
+// a group of solves of one shape: solve s takes the CTAs s * cps .. (s + 1) * cps - 1
+template <int L>
+__global__ void __launch_bounds__(32 * kZWarps) mode_z_warp_group_kernel(const __grid_constant__ ModeGroup g,
+                                                                          int groups, int cps) {
+  const int s = int(blockIdx.x) / cps;
+  const ModeArgs<float> a = g.args[s];
+  z_warp<L>(a, groups, int(blockIdx.x) % cps);
+}
+
+template <int L>
+cudaError_t launch_zw(const ModeArgs<float>& a, int groups, const ModeGroup* g, cudaStream_t st) {
   using Sh = ZWarpShape<L>;
   const int per = kZWarps * Sh::CPW;             // columns per CTA
+  const int cps = (a.mc + per - 1) / per;        // CTAs per solve
   void (*kern)(ModeArgs<float>, int) = mode_z_warp_kernel<L>;
+  void (*gkern)(const ModeGroup, int, int) = mode_z_warp_group_kernel<L>;
   if (Sh::SMEM > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM));
+    const cudaError_t e = g ? cudaFuncSetAttribute(gkern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM))
+                            : cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM));
     if (e != cudaSuccess) return e;
   }
-  kern<<<(a.mc + per - 1) / per, 32 * kZWarps, Sh::SMEM, st>>>(a, groups);
+  if (g) gkern<<<g->n * cps, 32 * kZWarps, Sh::SMEM, st>>>(*g, groups, cps);
+  else kern<<<cps, 32 * kZWarps, Sh::SMEM, st>>>(a, groups);
   return cudaGetLastError();
+}
+
+cudaError_t launch_zw_any(const ModeArgs<float>& a, int groups, const ModeGroup* g, cudaStream_t st) {
+  switch (a.nz) {
+    case 32: return launch_zw<32>(a, groups, g, st);
+    case 64: return launch_zw<64>(a, groups, g, st);
+    case 128: return launch_zw<128>(a, groups, g, st);
+    case 256: return launch_zw<256>(a, groups, g, st);
+    case 512: return launch_zw<512>(a, groups, g, st);
+    case 1024: return launch_zw<1024>(a, groups, g, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_mode_z_warp(const ModeArgs<float>& a, int groups, cudaStream_t st) {
-  switch (a.nz) {
-    case 32: return launch_zw<32>(a, groups, st);
-    case 64: return launch_zw<64>(a, groups, st);
-    case 128: return launch_zw<128>(a, groups, st);
-    case 256: return launch_zw<256>(a, groups, st);
-    case 512: return launch_zw<512>(a, groups, st);
-    case 1024: return launch_zw<1024>(a, groups, st);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_zw_any(a, groups, nullptr, st);
+}
+
+cudaError_t launch_mode_z_warp_group(const ModeArgs<float>& a, int groups, const ModeGroup& g, cudaStream_t st) {
+  if (g.n < 1 || g.n > kMaxModeGroup) return cudaErrorInvalidValue;
+  return launch_zw_any(a, groups, &g, st);
 }
 
 }  // namespace pp

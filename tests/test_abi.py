@@ -114,6 +114,10 @@ def test_status_fault_hook_and_batch_stream_entry_points_refuse_bad_arguments(L)
     assert L.pipe_batch_side_streams(hs, 1, None) == _lib.PIPE_EINVAL
     assert L.pipe_batch_select_streams(hs, 1, 2) == _lib.PIPE_EINVAL       # null handle
     assert L.pipe_batch_select_streams(hs, 0, 2) == _lib.PIPE_EINVAL       # empty set
+    assert L.pipe_batch_grouped(None, 1, ctypes.byref(n), None) == _lib.PIPE_EINVAL
+    assert L.pipe_batch_grouped(hs, 1, None, None) == _lib.PIPE_EINVAL
+    assert L.pipe_batch_select_groups(hs, 1, 1) == _lib.PIPE_EINVAL        # null handle
+    assert L.pipe_batch_select_groups(None, 1, 2) == _lib.PIPE_EINVAL
 
 
 def test_banded_setup_validation_without_gpu(L):

@@ -215,3 +215,39 @@ def test_batched_96_solve_mix_every_solve_against_oracle():
         if nx == 32:
             full = pipe.fft_solve(it["rho"], it["geom"], it["grid"], 1)
             assert np.linalg.norm(got - full) <= 1e-5 * np.linalg.norm(full)
+
+
+@pytest.mark.parametrize("nside", [0, 3])
+def test_batched_mode_groups_equal_loop_bitwise(nside):
+    """Mode-form solves of one shape and y-mode table in one launch per stage
+    (pipe_batch_select_groups): the same bits as single solves, on the
+    caller's stream or on side streams."""
+    from paper_1111_4971_gb300 import (PipeSolver, batch_grouped, batch_select, batch_select_groups,
+                                       batch_select_streams, batch_status, solve_batched)
+    items = bunches.workload_batched_96(seed=7, count=24)
+    solvers = [PipeSolver(it["geom"], it["grid"], igf=True, dtype=torch.float32) for it in items]
+    rhos = [torch.tensor(it["rho"], dtype=torch.float32, device="cuda") for it in items]
+    phis = [s.empty() for s in solvers]
+    solve_batched(solvers, rhos, phis)                    # tunes
+    loop = [s.solve(r) for s, r in zip(solvers, rhos)]
+    torch.cuda.synchronize()
+    nvar = 0
+    while True:                                           # the last variant: every solve outside
+        try:
+            batch_select(solvers, nvar + 1, 0)
+            nvar += 1
+        except Exception:
+            break
+    batch_select(solvers, nvar, 0)
+    batch_select_streams(solvers, nside)
+    batch_select_groups(solvers, True)
+    modes = sum(1 for s in solvers if s.plan["t_kind"] == 3)
+    assert batch_grouped(solvers) >= modes - 3            # at most one ungrouped solve per shape
+    out = [s.empty().fill_(7.0) for s in solvers]
+    solve_batched(solvers, rhos, out)
+    torch.cuda.synchronize()
+    assert batch_status(solvers) == 0
+    for a, b in zip(loop, out):
+        assert torch.equal(a, b)
+    batch_select_groups(solvers, False)
+    assert batch_grouped(solvers) == 0
