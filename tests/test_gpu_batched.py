@@ -251,3 +251,34 @@ def test_batched_mode_groups_equal_loop_bitwise(nside):
         assert torch.equal(a, b)
     batch_select_groups(solvers, False)
     assert batch_grouped(solvers) == 0
+
+
+def test_batched_mode_groups_keep_apart_what_differs():
+    """Solves share a group where the shape and the y-mode table agree: on a
+    cell-centred mesh spanning the pipe the table sin(n pi (j + 1/2) / ny)
+    does not depend on a, b or the Green function, so those mix; a different
+    mode count is a different table.  Every grouped result equals its single
+    solve bit for bit."""
+    from paper_1111_4971_gb300 import (PipeSolver, batch_grouped, batch_select, batch_select_groups,
+                                       batch_select_streams, solve_batched)
+    from inputs.bunches import cell_centred, gaussian_bunch
+    cases = []
+    for a, b, igf, modes in ((1.0, 1.0, 1, 20), (2.0, 1.0, 1, 20), (1.5, 1.0, 0, 12), (1.0, 0.5, 1, 20),
+                             (1.0, 0.5, 0, 12), (2.5, 1.0, 1, 20)):
+        geom, grid = cell_centred(a, b, 64, 64, 128, 0.04, modes=modes)
+        rho = gaussian_bunch(geom, grid, (a / 2, b / 2, 2.5), (0.15 * a, 0.15 * b, 0.6))
+        cases.append((geom, grid, igf, rho))
+    solvers = [PipeSolver(g, gr, igf=bool(i), dtype=torch.float32) for g, gr, i, _ in cases]
+    assert all(s.plan["t_kind"] == 3 for s in solvers)
+    rhos = [torch.tensor(r, dtype=torch.float32, device="cuda") for *_, r in cases]
+    solve_batched(solvers, rhos, [s.empty() for s in solvers])
+    batch_select(solvers, 1, 0)                        # one size: variant 1 leaves every solve outside
+    batch_select_streams(solvers, 0)
+    batch_select_groups(solvers, True)
+    grouped, groups = batch_grouped(solvers, with_groups=True)
+    # 20 modes: four solves (a, b and the Green function mixed); 12 modes: two
+    assert (grouped, groups) == (6, 2)
+    out = [s.empty().fill_(3.0) for s in solvers]
+    solve_batched(solvers, rhos, out)
+    for s, r, o in zip(solvers, rhos, out):
+        assert torch.equal(s.solve(r), o)
