@@ -249,6 +249,19 @@ def test_batched_mode_groups_equal_loop_bitwise(nside):
     assert batch_status(solvers) == 0
     for a, b in zip(loop, out):
         assert torch.equal(a, b)
+    # captured in a CUDA graph (the group's pointers are launch parameters) and replayed
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            solve_batched(solvers, rhos, out, stream=stream)
+    for _ in range(2):
+        for o in out:
+            o.fill_(5.0)
+        g.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(loop, out):
+            assert torch.equal(a, b)
     batch_select_groups(solvers, False)
     assert batch_grouped(solvers) == 0
 
