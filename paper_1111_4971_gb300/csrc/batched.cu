@@ -592,16 +592,26 @@ static int build_plan(pipe_handle* const* hs, int n, BatchPlan* b) {
   return PIPE_OK;
 }
 
-// one batched call with variant v: the persistent launch, then the solves
-// outside it, in order on stream st (nside = 0) or dealt round-robin to the
-// side streams, which start after the persistent launch and rejoin st; with
-// grp, each mode group's three launches take one slot of that order
+// one batched call with variant v: the persistent launch and the solves
+// outside it.  nside = 0: all in order on stream st.  Otherwise the side
+// streams fork from st, the persistent launch takes side stream 0 and the
+// outside solves are dealt round-robin to the side streams after it, so that
+// they run beside it; the side streams rejoin st.  (A persistent item waits
+// only for items handed out before it, which running CTAs hold, so kernels
+// beside it cannot stall it.)  With grp, each mode group's three launches
+// take one slot of that order.
 static int run_variant(BatchPlan* b, int v, int nside, int grp, pipe_handle* const* hs, const void* const* rho,
                        void* const* phi, cudaStream_t st) {
   BatchVariant& x = b->var[v];
-  int r = b->dtype == PIPE_F64 ? launch_variant<double>(&x, rho, phi, b->drop_stage, b->spin_limit, st)
-                               : launch_variant<float>(&x, rho, phi, b->drop_stage, b->spin_limit, st);
-  if (r != PIPE_OK || x.outside.empty()) return r;
+  auto persistent = [&](cudaStream_t s) {
+    return b->dtype == PIPE_F64 ? launch_variant<double>(&x, rho, phi, b->drop_stage, b->spin_limit, s)
+                                : launch_variant<float>(&x, rho, phi, b->drop_stage, b->spin_limit, s);
+  };
+  int r = PIPE_OK;
+  if (nside == 0 || x.outside.empty()) {
+    r = persistent(st);
+    if (r != PIPE_OK || x.outside.empty()) return r;
+  }
   std::vector<char> grouped(b->n, 0);
   if (grp)
     for (const MGroup& g : x.mgroups)
@@ -620,6 +630,10 @@ static int run_variant(BatchPlan* b, int v, int nside, int grp, pipe_handle* con
   for (int i = 0; i < nside; ++i)
     if (cudaStreamWaitEvent(b->side[i], b->fork, 0) != cudaSuccess) return PIPE_ECUDA;
   size_t slot = 0;
+  if (x.n > 0) {
+    r = persistent(b->side[0]);
+    slot = 1;
+  }
   if (grp)
     for (size_t k = 0; r == PIPE_OK && k < x.mgroups.size(); ++k)
       r = run_mode_group(x.mgroups[k], rho, phi, b->side[slot++ % nside]);
