@@ -18,6 +18,15 @@
 // warps (pipelined where the double buffer fits), transverse planes with the
 // cyclic-layout routine of the (1 CTA, 512 threads) plan; single solves with
 // that transverse plan give the same bits.
+//
+// The solves left outside the persistent launch run as their own launches,
+// on the caller's stream or dealt to side streams.  FP32 mode-space solves of
+// one shape and one y-mode table among them can run as a group: one launch
+// per stage (projection, z convolution, back-projection) for up to 64 solves,
+// each CTA finding its solve from its block index.  A stage of many solves is
+// a grid of many waves, so the reduction phase of some CTAs overlaps the
+// field streams of others.  The tuner times the persistent/outside split, the
+// work-list order, the side streams and the grouping, and keeps the fastest.
 #include <cuda_runtime.h>
 
 #include <cstring>
