@@ -355,22 +355,28 @@ def time_stages(stages, names, steps, flush, stream):
 
 def bench_batched(args, count=96):
     """96 independent IGF solves on mixed grids / aspect ratios: the batched
-    call (persistent launch plus the single-solve launches its tuner leaves
-    outside) replayed from a CUDA graph, against a loop of single solves."""
+    call (persistent launch, grouped mode-form launches and the single-solve
+    launches its tuner picks) replayed from a CUDA graph, against a loop of
+    single solves.  Each arm runs its own handles in its best configuration:
+    the loop with every handle autotuned for its single solve (which puts the
+    64^2 solves in the transform form), the batched call with the default
+    plans (the mode form wherever the modes are at most half the mesh),
+    which lets it group those solves as well."""
     import torch
 
     from inputs import bunches
     from paper_1111_4971_gb300 import (PipeSolver, batch_grouped, batch_plan_info, batch_side_streams, batch_status,
                                        solve_batched)
     items = bunches.workload_batched_96(count=count)
-    solvers, rhos = [], []
+    solvers, loop_solvers, rhos = [], [], []
     for it in items:
-        s = PipeSolver(it["geom"], it["grid"], igf=True, dtype=torch.float32)
-        solvers.append(s)
+        solvers.append(PipeSolver(it["geom"], it["grid"], igf=True, dtype=torch.float32))
+        loop_solvers.append(PipeSolver(it["geom"], it["grid"], igf=True, dtype=torch.float32))
         rhos.append(torch.tensor(it["rho"], dtype=torch.float32, device="cuda"))
     phis = [s.empty() for s in solvers]
+    loop_phis = [s.empty() for s in loop_solvers]
     grids = sorted({(it["grid"].nx, it["grid"].nz) for it in items})
-    for s in solvers:                   # autotuned plans for the loop of single solves
+    for s in loop_solvers:              # autotuned plans for the loop of single solves
         s.autotune()
     stream = torch.cuda.Stream()
     reps = max(5, args.steps // 4)
@@ -388,7 +394,7 @@ def bench_batched(args, count=96):
         return a.elapsed_time(b) / reps
 
     with torch.cuda.stream(stream):
-        loop_ms = timed(lambda: [s.solve(r, p, stream=stream) for s, r, p in zip(solvers, rhos, phis)])
+        loop_ms = timed(lambda: [s.solve(r, p, stream=stream) for s, r, p in zip(loop_solvers, rhos, loop_phis)])
         solve_batched(solvers, rhos, phis, stream=stream)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
@@ -398,7 +404,13 @@ def bench_batched(args, count=96):
     ok = batch_status(solvers) == 0
     persistent, order = batch_plan_info(solvers)
     grouped, ngroups = batch_grouped(solvers, with_groups=True)
+    # the two arms compute the same operator in their own forms: they agree to FP32 rounding
+    agree = max(float((a - b).norm() / b.norm()) for a, b in zip(phis, loop_phis))
+    forms = {"batched": sum(1 for s in solvers if s.plan["t_kind"] == 3),
+             "loop": sum(1 for s in loop_solvers if s.plan["t_kind"] == 3)}
     return {"solves": count, "grids": grids, "batched_ms": batch_ms, "loop_ms": loop_ms,
+            "plans": {"batched": "default", "loop": "autotuned per handle"},
+            "mode_form_solves": forms, "max_rel_l2_batched_vs_loop": agree,
             "batched_solves_per_s": count / (batch_ms * 1e-3),
             "loop_solves_per_s": count / (loop_ms * 1e-3), "speedup": loop_ms / batch_ms,
             "status_ok": ok, "persistent_solves": persistent,
