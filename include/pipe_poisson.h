@@ -268,7 +268,7 @@ int pipe_batch_select_streams(pipe_handle* const* handles, int n, int nside);
 
 /* Mode-form groups of the batched call: FP32 solves outside the persistent
  * launch that run the mode-space form with the occupancy-laid-out kernels
- * (pipe_get_plan t_kind 3 on a mesh symmetric in y, ny/2 in {16, 32, 64})
+ * (pipe_get_plan t_kind 3 on a mesh symmetric in y, ny/2 in {16, 32, 64, 128})
  * and share nx, ny, nz, the mode counts and the y-mode table run together:
  * one launch per stage for up to 64 solves, with the same kernels and the
  * same results, bit for bit, as their single-solve launches.  The tuner

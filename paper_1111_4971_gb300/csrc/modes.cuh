@@ -106,7 +106,7 @@ cudaError_t launch_mode_z_warp(const ModeArgs<float>& a, int groups, cudaStream_
 cudaError_t launch_mode_z_warp_group(const ModeArgs<float>& a, int groups, const ModeGroup& g, cudaStream_t st);
 
 // the FP32 projection and back-projection laid out for occupancy
-// (modes_fast.cu): meshes symmetric in y with ny/2 in {16, 32, 64}
+// (modes_fast.cu): meshes symmetric in y with ny/2 in {16, 32, 64, 128}
 bool mode_fast_ok(int ny, int nx, int myp, bool fy);
 // sy_host: the FP32 y-mode table [ny/2][myp] in host memory (the projection's parameter)
 cudaError_t launch_mode_fast(int stage, int myp, const ModeArgs<float>& a, const float* sy_host, cudaStream_t st);

@@ -1,5 +1,5 @@
 // FP32 projection and back-projection of the mode-space solve for meshes
-// symmetric in y with ny/2 in {16, 32, 64} rows per half: the same sums as
+// symmetric in y with ny/2 in {16, 32, 64, 128} rows per half: the same sums as
 // mode_project / mode_back (modes_impl.cuh), laid out for occupancy.
 //
 // A CTA of 16 warps covers 16 x rows and 32 consecutive z (one per lane), so
@@ -429,6 +429,7 @@ cudaError_t launch_fast_any(int stage, int myp, const ModeArgs<float>& a, const 
     case 16: return launch_fast2<16>(which, myp, a, g, sy_host, st);
     case 32: return launch_fast2<32>(which, myp, a, g, sy_host, st);
     case 64: return launch_fast2<64>(which, myp, a, g, sy_host, st);
+    case 128: return launch_fast2<128>(which, myp, a, g, sy_host, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -437,7 +438,7 @@ cudaError_t launch_fast_any(int stage, int myp, const ModeArgs<float>& a, const 
 
 bool mode_fast_ok(int ny, int nx, int myp, bool fy) {
   const int nyh = ny / 2;
-  return fy && (nyh == 16 || nyh == 32 || nyh == 64) && nx % kX == 0 &&
+  return fy && (nyh == 16 || nyh == 32 || nyh == 64 || nyh == 128) && nx % kX == 0 &&
          (myp == 8 || myp == 12 || myp == 16 || myp == 20 || myp == 24 || myp == 32);
 }
 
