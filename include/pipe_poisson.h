@@ -110,7 +110,8 @@ typedef struct pipe_handle pipe_handle;
  *    4096 each), nz in {32, ..., 1024} as above, modes_m, modes_n <= 32;
  *    PIPE_F32 or PIPE_F64; not banded; and its kernels' shared memory within
  *    the device's 227 KB per CTA (it grows with ny and the modes: FP32 with
- *    20 x 20 modes takes ny up to about 1400, FP64 about 700).  Its tables
+ *    20 x 20 modes takes ny up to about 1400, FP64 about 700; FP64 takes at
+ *    most about 880 mode pairs, e.g. 32 x 24 but not 32 x 32).  Its tables
  *    (FP64, with FP32 copies) take (nx*mxp + ny*myp + mxp*myp*(nz+1))*12
  *    bytes and its scratch (xblocks + 1)*mxp*myp*nz values of the dtype (the
  *    sizes of pipe_mode_layout).

@@ -270,3 +270,44 @@ def test_refusals():
     assert s40.plan["t_kind"] != 3
     with pytest.raises(PipeError):
         s40.set_plan(t_kind=3)
+
+
+@pytest.mark.parametrize("modes", [(1, 1), (1, 7), (32, 32), (5, 32)])
+def test_mode_counts_at_the_limits(modes):
+    """One mode, unequal counts, and the largest count the form takes
+    (32 per axis; in FP64 the back-projection's mode columns must fit in
+    shared memory, which 32 x 32 does not): solves and adjoints against O3."""
+    from paper_1111_4971_gb300 import PipeError
+    m, n = modes
+    geom = Geometry(1.3, 1.0, 1.3 / 64, 1.0 / 64, m, n)
+    grid = Grid(32, 32, 32, 1.3 / 32, 1.0 / 32, 0.05)
+    rho = _density(geom, grid, 71 + m + n)
+    for igf in (0, 1):
+        want = pipe.fft_solve(rho, geom, grid, igf)
+        for dtype, tol in ((torch.float64, F64_TOL), (torch.float32, F32_TOL)):
+            if dtype == torch.float64 and m * n > 880:
+                with pytest.raises(PipeError):
+                    mode_solver(geom, grid, igf, dtype)
+                continue
+            s = mode_solver(geom, grid, igf, dtype)
+            assert rel(host(s.solve(dev(rho, dtype))), want) <= tol, (modes, igf, dtype)
+            assert rel(host(s.adjoint(dev(rho, dtype))), want) <= tol, (modes, igf, dtype)
+
+
+def test_zero_density_and_point_charge():
+    """Zero in, zero out (every stage is linear); a unit charge on one node
+    against the oracle's exact sum at nodes near and far from it, on the
+    bench's own launch shapes (128^2 cell-centred, the fast FP32 kernels)."""
+    geom, grid = cell_centred(1.0, 1.0, 128, 128, 64, 0.02, modes=20)
+    for dtype in (torch.float64, torch.float32):
+        s = mode_solver(geom, grid, 1, dtype)
+        phi = s.solve(torch.zeros(grid.shape, dtype=dtype, device="cuda"))
+        assert torch.count_nonzero(phi).item() == 0
+    rho = np.zeros(grid.shape)
+    rho[40, 77, 31] = 1.0
+    nodes = [(40, 77, 31), (41, 77, 31), (40, 77, 33), (10, 100, 5), (127, 0, 63), (64, 64, 32)]
+    want = pipe.direct_sum_at(rho, geom, grid, 1, nodes)
+    for dtype, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        got = host(mode_solver(geom, grid, 1, dtype).solve(dev(rho, dtype)))
+        scale = np.abs(got).max()
+        assert np.abs(np.array([got[n] for n in nodes]) - want).max() <= tol * scale, dtype
