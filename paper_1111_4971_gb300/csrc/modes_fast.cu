@@ -218,6 +218,18 @@ __device__ __forceinline__ void project_fast(const ModeArgs<float>& a, const SyT
   cl.sync();
 }
 
+// d = a * b + c on both halves of a pair (the packed FP32 FMA of sm_100 and
+// later: one instruction for two FMAs, each rounded as fmaf)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 // rows j = J0 .. J0 + NJ - 1 of XR x rows (xs apart) and their mirrors
 // ny-1-j, the y-mode table read at compile-time offsets of the constant bank
 template <int NYH, int MYP, int XR, int J0, int NJ>
@@ -245,6 +257,43 @@ __device__ __forceinline__ void back_rows(const float (&bv)[XR][MYP], const SyTa
     for (int i = 0; i < XR; ++i) {
       lo[i * xs] = o[i] + e[i];
       hi[i * xs] = o[i] - e[i];
+    }
+    lo += nz;
+    hi -= nz;
+    // one running pointer per mirror, not one precomputed address per row
+    asm volatile("" : "+l"(lo), "+l"(hi));
+  }
+}
+
+// the same with bv[i][p] holding slots 2p and 2p + 1, summed as pairs by packed FMAs (MYP / 2
+// is even, so no pair straddles the odd and even halves)
+template <int NYH, int MYP, int XR, int J0, int NJ>
+__device__ __forceinline__ void back_rows2(const float2 (&bv)[XR][MYP / 2], const SyTab<NYH, MYP>& tab, float* base,
+                                          int nz, int xs) {
+  constexpr int H = MYP / 2;
+  static_assert(H % 2 == 0, "slot pairs must not straddle the odd and even halves");
+  float* lo = base + J0 * nz;
+  float* hi = base + (2 * NYH - 1 - J0) * nz;
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj) {
+    const int j = J0 + jj;
+    float2 o[XR], e[XR];
+#pragma unroll
+    for (int i = 0; i < XR; ++i) o[i] = e[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int p = 0; p < MYP / 2; ++p) {
+      const float2 s = make_float2(tab.s[j * MYP + 2 * p], tab.s[j * MYP + 2 * p + 1]);
+#pragma unroll
+      for (int i = 0; i < XR; ++i) {
+        if (2 * p < H) o[i] = ffma2(s, bv[i][p], o[i]);
+        else e[i] = ffma2(s, bv[i][p], e[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < XR; ++i) {
+      const float os = o[i].x + o[i].y, es = e[i].x + e[i].y;
+      lo[i * xs] = os + es;
+      hi[i * xs] = os - es;
     }
     lo += nz;
     hi -= nz;
@@ -315,19 +364,36 @@ __device__ __forceinline__ void back_fast(const ModeArgs<float>& a, const SyTab<
   // XR x rows a thread: two (the two warps of an x pair split the rows j)
   // up to 20 y-mode slots, else one (a warp takes all rows j of its x row)
   constexpr int XR = back_rows_per_thread<MYP>();
-  float bv[XR][MYP];
   const int x0 = XR == 2 ? 2 * pair : warp;
-#pragma unroll
-  for (int i = 0; i < XR; ++i)
-#pragma unroll
-    for (int n = 0; n < MYP; ++n) bv[i][n] = bvs[(x0 + i) * BS + n * kZC + lane];
   float* base = a.phi + size_t(xb0 + x0) * ny * a.nz + z0 + lane;
-  if (XR == 1)
-    back_rows<NYH, MYP, XR, 0, NYH>(bv, tab, base, a.nz, ny * a.nz);
-  else if (half == 0)
-    back_rows<NYH, MYP, XR, 0, NYH / 2>(bv, tab, base, a.nz, ny * a.nz);
-  else
-    back_rows<NYH, MYP, XR, NYH / 2, NYH / 2>(bv, tab, base, a.nz, ny * a.nz);
+  if constexpr (NYH <= 64) {
+    // packed FMAs over slot pairs (at ny/2 = 128 the longer unrolled row
+    // loop spills with them, so that size keeps one FMA per slot)
+    float2 bv[XR][MYP / 2];
+#pragma unroll
+    for (int i = 0; i < XR; ++i)
+#pragma unroll
+      for (int p = 0; p < MYP / 2; ++p)
+        bv[i][p] = make_float2(bvs[(x0 + i) * BS + 2 * p * kZC + lane], bvs[(x0 + i) * BS + (2 * p + 1) * kZC + lane]);
+    if (XR == 1)
+      back_rows2<NYH, MYP, XR, 0, NYH>(bv, tab, base, a.nz, ny * a.nz);
+    else if (half == 0)
+      back_rows2<NYH, MYP, XR, 0, NYH / 2>(bv, tab, base, a.nz, ny * a.nz);
+    else
+      back_rows2<NYH, MYP, XR, NYH / 2, NYH / 2>(bv, tab, base, a.nz, ny * a.nz);
+  } else {
+    float bv[XR][MYP];
+#pragma unroll
+    for (int i = 0; i < XR; ++i)
+#pragma unroll
+      for (int n = 0; n < MYP; ++n) bv[i][n] = bvs[(x0 + i) * BS + n * kZC + lane];
+    if (XR == 1)
+      back_rows<NYH, MYP, XR, 0, NYH>(bv, tab, base, a.nz, ny * a.nz);
+    else if (half == 0)
+      back_rows<NYH, MYP, XR, 0, NYH / 2>(bv, tab, base, a.nz, ny * a.nz);
+    else
+      back_rows<NYH, MYP, XR, NYH / 2, NYH / 2>(bv, tab, base, a.nz, ny * a.nz);
+  }
 }
 
 // one solve: grid (nz / 32, nx / 16)

@@ -125,31 +125,40 @@ __device__ __forceinline__ void z_warp(const ModeArgs<float>& a, int groups, int
     for (int k2 = 0; k2 < S; ++k2) T[b + S * i + E * k2] = v[i * S + k2];
   __syncwarp();
 
-  // 3. real spectrum, kernel product, packed inverse input Z'(k), k = b + S i,
-  //    into the column's second buffer (a rolled loop: the code stays small
-  //    enough for the instruction cache), then back to registers
+  // 3. real spectrum, kernel product, packed inverse input Z'(k) into the
+  //    column's second buffer, then back to registers in the layout of the
+  //    inverse.  Each pair (k, L-k), k = b + S i < L/2, is formed once:
+  //    with s = Y(k) + conj Y(L-k) and t = conj(w^k) (Y(k) - conj Y(L-k)),
+  //    Z'(k) = s + i t and Z'(L-k) = conj(s) + i conj(t); lane b = 0 also
+  //    takes the self-paired k = L/2.  (A rolled loop: the code stays small
+  //    enough for the instruction cache.)
   const float* g = gs + cl * (L + 1);
   V* U = T + Sh::CB;
-#pragma unroll 2
-  for (int i = 0; i < E; ++i) {
-    const int k = b + S * i;
+  auto pair = [&](int k, bool both) {
     const V zk = T[k], zm = T[(L - k) & (L - 1)];
     const V wk = wks[k];                         // w^k
     const V wm = make_float2(-wk.x, wk.y);       // w^{L-k} = -conj(w^k)
     const float gk = valid ? g[k] : 0.f, gm = valid ? g[L - k] : 0.f;
     auto unpack = [](V x, V xm, V w) {           // (x + conj xm - i w (x - conj xm)) / 2
       const V c = cconj(xm);
-      const V s = cadd(x, c), d = csub(x, c);
-      const V wd = cmul(w, d);
-      return make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
+      const V su = cadd(x, c), df = csub(x, c);
+      const V wd = cmul(w, df);
+      return make_float2(0.5f * (su.x + wd.y), 0.5f * (su.y - wd.x));
     };
     const V yk = cscale(unpack(zk, zm, wk), gk);
     const V ym = cscale(unpack(zm, zk, wm), gm);
-    const V c = cconj(ym);                       // yk + conj ym + i conj(w^k) (yk - conj ym)
-    const V s = cadd(yk, c), d = csub(yk, c);
-    const V wd = cmulc<true>(d, wk);
-    U[k] = make_float2(s.x - wd.y, s.y + wd.x);
+    const V c = cconj(ym);
+    const V sp = cadd(yk, c), d = csub(yk, c);
+    const V t = cmulc<true>(d, wk);
+    U[k] = make_float2(sp.x - t.y, sp.y + t.x);
+    if (both) U[L - k] = make_float2(sp.x + t.y, t.x - sp.y);
+  };
+#pragma unroll 2
+  for (int i = 0; i < E / 2; ++i) {
+    const int k = b + S * i;
+    pair(k, k != 0);
   }
+  if (b == 0) pair(L / 2, false);
   __syncwarp();
 #pragma unroll
   for (int i = 0; i < E; ++i) v[i] = U[b + S * i];
