@@ -331,8 +331,8 @@ int pipe_stage_z_inverse(pipe_handle* h, const void* spec, void* phi, int adjoin
  * otherwise *fold = 0 and slot s holds n = s+1 (slots beyond modes_n are
  * zero).  Mode column c = (m-1)*myp + slot.  xblocks: the groups of x rows
  * whose projections the first stage writes separately (the kernel works on
- * blocks of 16 rows in FP32, 8 in FP64, and sums up to 8 neighbouring blocks
- * in a thread-block cluster; xblocks = blocks / that cluster size, 1 for
+ * blocks of 16 rows in FP32, 8 in FP64, and sums up to 4 neighbouring blocks
+ * in a thread-block cluster; xblocks = blocks / that cluster size, 2 for
  * FP32 nx = 128).  Errors: PIPE_EINVAL (null pointers), PIPE_EUNSUPPORTED
  * (the mode-space form cannot take the handle). */
 int pipe_mode_layout(pipe_handle* h, int* mx, int* mxp, int* myp, int* fold, int* xblocks);

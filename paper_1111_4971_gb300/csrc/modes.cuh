@@ -73,10 +73,12 @@ inline int mode_of_slot(int s, int myp, bool fold) {
 }
 
 // CTAs per cluster of the projection: the largest divisor of its x blocks
-// that is at most 8 (the portable cluster size); the projection writes
-// xblocks / mode_cluster(xblocks) partial sums
+// that is at most 4; the projection writes xblocks / mode_cluster(xblocks)
+// partial sums, which the z convolution adds on load.  (Clusters of 8, one
+// partial at 128 x rows, kept every CTA in the distributed-shared-memory
+// reduction longer than the second partial costs the z kernel.)
 inline int mode_cluster(int xblocks) {
-  for (int d = 8; d > 1; --d)
+  for (int d = 4; d > 1; --d)
     if (xblocks % d == 0) return d;
   return 1;
 }

@@ -90,7 +90,7 @@ __device__ __forceinline__ void z_warp(const ModeArgs<float>& a, int groups, int
 #pragma unroll
   for (int i = 0; i < E; ++i) v[i] = make_float2(0.f, 0.f);
   if (valid) {
-#pragma unroll 1
+#pragma unroll 4
     for (int s = 0; s < groups; ++s) {
       const V* src = reinterpret_cast<const V*>(a.part + (size_t(s) * a.mc + col) * L) + b;
 #pragma unroll
