@@ -199,7 +199,7 @@ int pipe_poisson_adjoint(pipe_handle* h, const void* dphi, void* drho, void* str
  * (null or misaligned pointers), PIPE_EUNSUPPORTED when the buffer exceeds
  * 64 MiB (e.g. 128x128x256 FP32 in the transform form fits, 128x128x512 does
  * not; the mode-space form of 128x128x1024 FP32 with 20 x 20 modes takes
- * 3.3 MB), or for banded, complex-FP16 or window (transform form) handles,
+ * 4.9 MB), or for banded, complex-FP16 or window (transform form) handles,
  * PIPE_ECUDA. */
 int pipe_poisson_solve_noalloc(pipe_handle* h, const void* rho, void* phi, void* stream);
 
