@@ -18,7 +18,8 @@
 //                    the sums of Sy[j][n] B[x][n][z] over odd and even n, the
 //                    table again a kernel parameter; a thread holds the B values
 //                    of two x rows (up to 20 y-mode slots; the two warps of an x
-//                    pair split the rows j) or of one.
+//                    pair split the rows j) or of one, and sums slot pairs with
+//                    the packed FP32 FMA (fma.rn.f32x2) where ny/2 <= 64.
 //
 // The two x-mode sums are small matrix products per CTA, [(n, z)] x [x] by
 // [x] x [m] and [(n, z)] x [m] by [m] x [x], and run on the tensor cores as
@@ -30,7 +31,9 @@
 // (g+8, t+4); B (8 x 8, column major) (t, g), (t+4, g); C (16 x 8) (g, 2t),
 // (g, 2t+1), (g+8, 2t), (g+8, 2t+1).  A tile's 16 rows are 16 z of one n; the
 // shared-memory rows are padded so that the fragment reads and writes of a
-// warp fall on 32 distinct banks.
+// warp fall on 32 distinct banks.  (The same products on tcgen05 were slower:
+// with K = 16 x rows per CTA, staging the operands in K-major core matrices
+// costs more than the faster tensor pipe saves.)
 #include "modes.cuh"
 #include "modes_impl.cuh"
 
