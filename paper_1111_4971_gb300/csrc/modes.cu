@@ -1,5 +1,7 @@
 // Kernels and host launchers of the mode-space solve (the method and the
 // device routines are described in modes_impl.cuh).
+#include <type_traits>
+
 #include "modes.cuh"
 #include "modes_impl.cuh"
 
@@ -35,13 +37,25 @@ __global__ void __launch_bounds__(kBandThreads) mode_band_kernel(ModeArgs<T> a, 
   T* win = reinterpret_cast<T*>(smem_raw);           // [nz + 2 nb]: win[nb + k] = rhot[k]
   T* taps = win + a.nz + 2 * a.nb;                   // [nb + 1]
   const int c = int(blockIdx.x);
-  const int nw = a.nz + 2 * a.nb;
-  for (int i = int(threadIdx.x); i < nw; i += kBandThreads) {
-    const int k = i - a.nb;
-    T v = T(0);
-    if (k >= 0 && k < a.nz)
-      for (int s = 0; s < groups; ++s) v += a.part[(size_t(s) * a.mc + c) * a.nz + k];
-    win[i] = v;
+  for (int i = int(threadIdx.x); i < a.nb; i += kBandThreads) win[i] = win[a.nb + a.nz + i] = T(0);
+  // the column summed over the groups (in group order, from zero), 16 bytes a
+  // load, every group's load of a piece in flight together (nz is a power of
+  // two >= 32, so the pieces tile it and stay 16-byte aligned)
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int EV = 16 / sizeof(T);
+  for (int q = int(threadIdx.x); q < a.nz / EV; q += kBandThreads) {
+    T v[EV];
+#pragma unroll
+    for (int e = 0; e < EV; ++e) v[e] = T(0);
+#pragma unroll 4
+    for (int s = 0; s < groups; ++s) {
+      const V p = __ldg(reinterpret_cast<const V*>(a.part + (size_t(s) * a.mc + c) * a.nz) + q);
+      const T* pe = reinterpret_cast<const T*>(&p);
+#pragma unroll
+      for (int e = 0; e < EV; ++e) v[e] += pe[e];
+    }
+#pragma unroll
+    for (int e = 0; e < EV; ++e) win[a.nb + q * EV + e] = v[e];
   }
   for (int d = int(threadIdx.x); d <= a.nb; d += kBandThreads) taps[d] = a.kb[size_t(c) * (a.nb + 1) + d];
   __syncthreads();
