@@ -128,3 +128,49 @@ def test_real_to_complex_pairs_of_the_padded_z_transform(nz):
         assert abs(X[k] - r2c(zk, zm, w ** k)) < 1e-11 * scale
         assert abs(X[nz - k] - r2c(zm, zk, -np.conj(w ** k))) < 1e-11 * scale
     assert abs(X[nz] - (Z[0].real - Z[0].imag)) < 1e-11 * scale
+
+
+@pytest.mark.parametrize("nz", [32, 256, 1024])
+def test_mode_z_convolution_by_spectral_pairs(nz):
+    """The z convolution of one mode column as the warp kernel forms it, against
+    its plain definition psi[k] = sum_{k' < nz} K(|k - k'|) rho[k'] (K real).
+
+    Z is the nz-point DFT of the packed column z_m = rho_{2m} + i rho_{2m+1}
+    (m < nz/2, zero beyond: Appendix A's padding), g the 2nz-point DFT of the
+    doubled table K(0..nz), K(nz-1..1) divided by 2nz (real and even).  For each
+    pair (k, nz - k), k <= nz/2, with X as in the test above,
+      Y(k) = g(k) X(k),  Y(nz - k) = g(nz - k) X(nz - k),
+      s = Y(k) + conj Y(nz - k),  t = conj(w^k) (Y(k) - conj Y(nz - k)),
+      U(k) = s + i t,  U(nz - k) = conj(s) + i conj(t),
+    and the unnormalised inverse p_m = sum_k U(k) e^{2 pi i k m / nz} gives
+    psi_{2m} + i psi_{2m+1} = p_m for m < nz/2."""
+    rng = np.random.default_rng(7 + nz)
+    rho = rng.standard_normal(nz)
+    K = rng.standard_normal(nz + 1)
+    d = np.abs(np.arange(nz)[:, None] - np.arange(nz)[None, :])
+    psi = (K[d] * rho[None, :]).sum(axis=1)
+    G = np.fft.fft(np.concatenate([K, K[nz - 1:0:-1]]))
+    assert np.abs(G.imag).max() < 1e-9 * np.abs(G).max()
+    g = G.real / (2 * nz)
+    z = np.zeros(nz, complex)
+    z[: nz // 2] = rho[0::2] + 1j * rho[1::2]
+    Z = np.fft.fft(z)
+    w = np.exp(-1j * np.pi / nz)
+
+    def unpack(x, xm, wk):
+        c = np.conj(xm)
+        return ((x + c) - 1j * wk * (x - c)) / 2
+
+    U = np.zeros(nz, complex)
+    for k in range(nz // 2 + 1):
+        zk, zm, wk = Z[k % nz], Z[(nz - k) % nz], w ** k
+        yk = g[k] * unpack(zk, zm, wk)
+        ym = g[nz - k] * unpack(zm, zk, -np.conj(wk))
+        s, t = yk + np.conj(ym), np.conj(wk) * (yk - np.conj(ym))
+        U[k % nz] = s + 1j * t
+        if 0 < k < nz // 2:
+            U[nz - k] = np.conj(s) + 1j * np.conj(t)
+    p = np.fft.ifft(U) * nz
+    got = np.empty(nz)
+    got[0::2], got[1::2] = p[: nz // 2].real, p[: nz // 2].imag
+    assert np.abs(got - psi).max() < 1e-10 * np.abs(psi).max()
