@@ -87,3 +87,22 @@ def test_replica_launch_spawns_or_refuses_on_a_mismatch():
     assert bench.replica_launch(2, {"WORLD_SIZE": "2"}) == ("run", None)
     how, msg = bench.replica_launch(8, {"WORLD_SIZE": "1"})
     assert how == "error" and "WORLD_SIZE=1" in msg
+
+
+def test_roofline_bytes_and_recorded_traffic(monkeypatch):
+    """The mode form's algorithmic bytes per launch, and the DRAM traffic of a
+    committed ncu summary reported only while its kernel sources hash to the
+    value written beside it."""
+    import bench
+    field, mc, nz = 128 * 128 * 1024 * 4, 400, 1024
+    b = bench.mode_alg_bytes(128, 128, 1024, mc, 2)
+    assert b["mode_project"] == field + 2 * mc * nz * 4
+    assert b["mode_z"] == 2 * mc * nz * 4 + mc * (nz + 1) * 4 + mc * nz * 4
+    assert b["mode_back"] == mc * nz * 4 + field
+    monkeypatch.setattr(bench, "source_hash", lambda k: "0000000000000000")
+    assert bench.recorded_traffic("mode_project") is None
+    path = bench.os.path.join(bench.ROOT, "profiles", bench.PROFILE_FILES["mode_project"])
+    text = open(path).read()
+    recorded = text.split("mode_project_source_sha256: `")[1].split("`")[0]
+    monkeypatch.setattr(bench, "source_hash", lambda k: recorded)
+    assert bench.recorded_traffic("mode_project") > 0
